@@ -1,0 +1,182 @@
+/*
+ * dagrt.h -- C ABI of libdagrt, a GB300 (sm_103a) library that evaluates the makespan
+ * bound of "Exploiting Dependency and Parallelism: Real-Time Scheduling and Analysis for
+ * GPU Tasks" (DAC '26) for batches of DAG-structured GPU tasks and candidate schedules.
+ *
+ * Problem statement (System Model, Sec. 2): a task is a DAG G = (V, E) whose nodes are
+ * kernels v_i = {C^_i, C_i, m_i}: C^_i is the computation load (execution time on one SM,
+ * integer ticks), m_i the SMs it is given and C_i its execution time (Eq.1); the GPU has M
+ * SMs. The scheduler (Alg.1 Sub-graph_Division, Alg.2 Scheduling) chooses m_i, splits
+ * nodes into segments and adds extra dependency edges; Lemma 1 and Theorem 1 bound the
+ * makespan: R(G) <= sum_j max_{v_i in pi_j} C_i.
+ *
+ * Integer semantics (no floating point enters any bound; all times are int64 ticks):
+ *   C(x, k, m) = max(1, ceil( ceil(m/M) * x * (64m - k(m-1)) / (64m) ))
+ * is Eq.1 with t_min = 1, rounded up, and a per-kernel parallel fraction f = k/64 applied
+ * as Amdahl's law; k = 64 gives Eq.1 exactly.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns DAGRT_OK (0) or a negative DAGRT_E_* code and never aborts; the
+ *    message of the last failure is available from dagrt_last_error().
+ *  - All device work is enqueued on the context's stream in order. Calls given host
+ *    pointers copy through device staging buffers and synchronise that stream before they
+ *    return. Calls given device pointers (DAGRT_PTR_DEVICE) only enqueue work; their
+ *    outputs are valid once the caller synchronises the stream.
+ *  - The caller owns every buffer it passes; the library owns the staging and scratch
+ *    memory inside a context and a batch, and frees it in dagrt_destroy/dagrt_batch_free.
+ */
+#ifndef DAGRT_H
+#define DAGRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define DAGRT_OK 0
+#define DAGRT_E_INVAL (-1)    /* null pointer, M outside [1, 4096], bad offsets or row_ptr,
+                                 C^ outside [1, 2^32-1], k > 64, unknown variant/flag */
+#define DAGRT_E_CYCLE (-2)    /* the graph of some DAG has a cycle */
+#define DAGRT_E_RANGE (-3)    /* successor id outside [0, V), self loop, or a successor list
+                                 that is not strictly increasing (duplicates included) */
+#define DAGRT_E_OOM (-4)      /* device or pinned-host allocation failed */
+#define DAGRT_E_DEVICE (-5)   /* a CUDA call failed */
+#define DAGRT_E_TIMEOUT (-6)  /* reserved: a bounded device loop gave up */
+#define DAGRT_E_CAP (-7)      /* an output buffer was smaller than the result (counts are
+                                 still written) */
+#define DAGRT_E_INTERNAL (-8) /* a device-side consistency check failed */
+
+/* ---------------------------------------------------------------- flags */
+#define DAGRT_PTR_DEVICE 1u   /* the call's array arguments are device pointers */
+
+/* ---------------------------------------------------------------- structure variants
+ * The schedule structure (groups, parallel launches, segments, extra edges) a bound is
+ * evaluated on. DAGRT_VAR_PAPER is Alg.2 as the paper describes it, reading "S_j remaining
+ * SMs" (Eq.6) as SMs still free after each launch. */
+#define DAGRT_VAR_PAPER 0     /* Alg.1 groups; Alg.2 with parallel launches and segmentation */
+#define DAGRT_VAR_NOPARA 1    /* Alg.1 groups; Eq.5 only, no parallel-node launches */
+#define DAGRT_VAR_NOSEG 2     /* parallel launches of nodes that fit; never segments */
+#define DAGRT_VAR_LITERAL 3   /* Alg.2 with S_j fixed per group and WS_j <- WS_j - C^_c */
+#define DAGRT_N_VARIANTS 4
+
+/* ---------------------------------------------------------------- limits */
+#define DAGRT_MAX_M 4096
+#define DAGRT_MAX_V 65535     /* nodes per DAG */
+
+typedef struct dagrt_ctx dagrt_ctx;
+typedef struct dagrt_batch dagrt_batch;
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t (for example a
+ * torch stream's handle) or NULL for the legacy default stream. Returns DAGRT_E_DEVICE if
+ * the device cannot be used. *out receives the context (NULL on failure). */
+int dagrt_create(dagrt_ctx **out, int device, void *cuda_stream);
+
+/* Change the stream later calls enqueue on. */
+int dagrt_set_stream(dagrt_ctx *ctx, void *cuda_stream);
+
+/* Synchronise the context's stream and report any CUDA error seen on it. */
+int dagrt_sync(dagrt_ctx *ctx);
+
+/* Free a context and every device buffer it owns. Batches created from it must be freed
+ * first. NULL is ignored. */
+void dagrt_destroy(dagrt_ctx *ctx);
+
+/* Text of the last error on this context ("" if none). Valid until the next call. */
+const char *dagrt_last_error(const dagrt_ctx *ctx);
+
+/* Load a batch of n_dags DAGs (System Model, Sec. 2.1: G = (V, E), C^_i; plus the
+ * parallel fraction k_i/64 of each kernel) for an M-SM GPU (Sec. 2).
+ *   node_off[n_dags+1] int64  DAG d owns nodes node_off[d] .. node_off[d+1]-1
+ *                             (V_d <= DAGRT_MAX_V; V_d = 0 is an empty DAG)
+ *   edge_off[n_dags+1] int64  DAG d owns edges edge_off[d] .. edge_off[d+1]-1
+ *   row_ptr[total_nodes + n_dags] int32  successor CSR of DAG d: its V_d+1 entries start
+ *                             at node_off[d] + d, are local to edge_off[d], start at 0,
+ *                             never decrease and end at E_d
+ *   col[total_edges] int32    DAG-local successor ids, strictly increasing per row
+ *   wcet[total_nodes] int64   C^_i in [1, 2^32-1] ticks
+ *   k64[total_nodes] uint8    k_i in [0, 64]
+ * With DAGRT_PTR_DEVICE the arrays are device pointers that the batch reads in place and
+ * that must stay valid and unchanged until dagrt_batch_free; otherwise they are host
+ * pointers that are copied. The offsets are checked here (E_INVAL); per-DAG graph checks
+ * run on the device inside dagrt_schedule and are reported there, per DAG. */
+int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off,
+                   const int64_t *edge_off, const int32_t *row_ptr, const int32_t *col,
+                   const int64_t *wcet, const uint8_t *k64, int32_t M, uint32_t flags,
+                   dagrt_batch **out);
+
+/* Free a batch (NULL is ignored). Waits for the batch's work on the context stream. */
+void dagrt_batch_free(dagrt_batch *batch);
+
+int32_t dagrt_batch_n_dags(const dagrt_batch *batch);
+int64_t dagrt_batch_total_nodes(const dagrt_batch *batch);
+
+/* Outputs of dagrt_schedule. Every pointer may be NULL (not written). Per-node arrays are
+ * indexed like wcet (node_off[d] + v); per-group and per-segment arrays of DAG d start at
+ * node_off[d] (a DAG has at most V_d groups and V_d segments); plan rows of DAG d start at
+ * 2*node_off[d]. Segment s of DAG d has the expanded-node id V_d + s. */
+typedef struct {
+    int64_t *bound;      /* [n_dags] R(G), Theorem 1; -1 where status != 0 */
+    int32_t *status;     /* [n_dags] DAGRT_OK or the DAG's E_INVAL/E_RANGE/E_CYCLE/E_CAP */
+    int32_t *n_groups;   /* [n_dags] |Pi| of Alg.1 (dropped groups included) */
+    int32_t *n_seg;      /* [n_dags] segments made by Alg.2 */
+    int32_t *n_rows;     /* [n_dags] plan rows (= V_d + n_seg) */
+    int64_t *n_extra;    /* [n_dags] extra dependency edges of Alg.2 */
+    int32_t *level;      /* [nodes] topological level: 0 for sources, 1 + max over preds */
+    int64_t *wanc;       /* [nodes] W^anc, Eq.2 */
+    int32_t *block_of;   /* [nodes] index k of B_k (Eq.3; k = index of theta_k in Theta),
+                            or |Theta| for the residual block */
+    int32_t *group_of;   /* [nodes] index of the node's balanced group in Pi (Alg.1) */
+    int32_t *exec_group; /* [nodes] group during which the node's last part runs (Alg.2) */
+    int32_t *m;          /* [nodes] SMs of the node's last part (Eq.5 or a parallel launch) */
+    int64_t *group_R;    /* [groups] R(pi_j) per group (Lemma 1), 0 for a dropped group */
+    int32_t *seg_parent; /* [segments] node split by the node-segmentation step */
+    int64_t *seg_load;   /* [segments] load of the parallel segment */
+    int32_t *seg_m;      /* [segments] its SMs */
+    int32_t *seg_group;  /* [segments] group it runs in */
+    int32_t *row_id;     /* [rows] node id (< V_d) or segment id (>= V_d) */
+    int32_t *row_group;  /* [rows] group it runs in; rows are ordered by group, members by
+                            id first, then parallel launches in launch order */
+    int32_t *row_m0;     /* [rows] scheduled SMs */
+    int64_t *row_load;   /* [rows] load executed by the row */
+    int64_t *extra_off;  /* [n_dags+1] capacity layout of the extra-edge buffers (host or
+                            device like the others); NULL = do not write edges */
+    int32_t *extra_src;  /* [extra_off[n_dags]] (v_R, v_n) and (v_n, succ(v_R)) edges */
+    int32_t *extra_dst;
+} dagrt_schedule_out;
+
+/* Run Alg.1 and Alg.2 with structure variant `variant` on every DAG of the batch, evaluate
+ * the bound of the resulting schedule (Lemma 1, Theorem 1) and keep the schedule in the
+ * batch as the plan that dagrt_bound evaluates candidate allocations on.
+ * flags: DAGRT_PTR_DEVICE if the `out` pointers are device pointers.
+ * Returns the first failing DAG's status (E_INVAL, E_RANGE, E_CYCLE, E_CAP), or a device
+ * error; with device outputs the per-DAG status array is the only report and the return
+ * value covers launch errors only. */
+int dagrt_schedule(dagrt_batch *batch, int32_t variant, const dagrt_schedule_out *out,
+                   uint32_t flags);
+
+/* Bound of candidate allocations on fixed schedule structures (Lemma 1 / Theorem 1 on a
+ * schedule whose SMs per node are given): per group, max C_i if the group's SMs fit in M,
+ * else sum C_i (the sequential assumption of the Greedy analysis, Sec. 5.2); the bound is
+ * the sum over groups (a max-plus sweep along the group chain).
+ *   variant_ids[n_variants]  structure variant of each candidate block; each must have
+ *                            been scheduled on this batch with dagrt_schedule
+ *   n_alloc                  allocations per variant; candidate c = v*n_alloc + a
+ *   m_alloc                  uint8 SMs per plan row and candidate, laid out
+ *                            [(2*node_off[d] + row) * cand_stride + c]; 0 = keep the
+ *                            scheduled m of the row
+ *   cand_stride              >= n_variants*n_alloc and a multiple of 16
+ *   out_bound                [n_dags * n_cand] int64 (may be NULL)
+ *   best_bound, best_cand    [n_dags] argmin over candidates (smallest bound, then
+ *                            smallest candidate id); may be NULL
+ * flags: DAGRT_PTR_DEVICE if all array arguments are device pointers. */
+int dagrt_bound(dagrt_batch *batch, int32_t n_variants, const int32_t *variant_ids,
+                int32_t n_alloc, const uint8_t *m_alloc, int64_t cand_stride,
+                int64_t *out_bound, int64_t *best_bound, int32_t *best_cand, uint32_t flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAGRT_H */

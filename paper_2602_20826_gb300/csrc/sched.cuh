@@ -1,0 +1,47 @@
+// sched.cuh -- host-visible interface of the scheduling kernels (sched.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/dagrt.h"
+
+namespace dagrt {
+
+constexpr int kWarpsPerCta = 4;    // independent warp teams per CTA (small DAGs)
+constexpr int kCtaThreads = 256;   // threads of a CTA team (large DAGs)
+
+// Arguments of one scheduling launch. Every pointer is a device pointer.
+struct SchedArgs {
+    const int64_t *node_off;
+    const int64_t *edge_off;
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const int64_t *wcet;
+    const uint8_t *k64;
+    int32_t M;
+    int32_t variant;
+    // DAGs of this size class and the work-stealing counter over them
+    const int32_t *list;
+    int32_t n_list;
+    int32_t *counter;
+    // always written: per-DAG status, bound, plan row count; plan rows at 2*node_off[d]
+    int32_t *status;
+    int64_t *bound;
+    int32_t *nrows;
+    uint2 *plan_lc;      // {load, scheduled C}
+    uint32_t *plan_mkf;  // m | k << 16 | last-row-of-group << 24
+    // optional caller outputs (device pointers, NULL = skip)
+    dagrt_schedule_out o;
+    // global workspace of the CTA-team kernel
+    unsigned char *gws;
+    int64_t gws_stride;
+    int32_t vcap;
+};
+
+int64_t sched_ws_bytes(int vc);
+cudaError_t sched_launch_warp(int vc, const SchedArgs &a, int n_sm, cudaStream_t st);
+int sched_cta_grid(int n_sm);
+cudaError_t sched_launch_cta(const SchedArgs &a, int grid, cudaStream_t st);
+
+}  // namespace dagrt

@@ -1,0 +1,225 @@
+"""Thin Python binding of libdagrt's C ABI (include/dagrt.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels. The raw entry points keep their C names (`dagrt_create`, `dagrt_load_csr`,
+`dagrt_schedule`, `dagrt_bound`, ...); `Context` and `LoadedBatch` wrap them for numpy
+(host) arrays and torch CUDA tensors (device pointers, used in place).
+
+Importing this module loads `libdagrt.so` built in-tree by `build.py`; it raises
+ImportError when the library is missing. There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libdagrt.so is not built ({_LIB_PATH}); run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'` first")
+lib = C.CDLL(_LIB_PATH)
+
+OK, E_INVAL, E_CYCLE, E_RANGE, E_OOM, E_DEVICE, E_TIMEOUT, E_CAP, E_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7, -8
+PTR_DEVICE = 1
+VAR_PAPER, VAR_NOPARA, VAR_NOSEG, VAR_LITERAL = 0, 1, 2, 3
+MAX_M, MAX_V = 4096, 65535
+
+_vp = C.c_void_p
+
+
+class dagrt_schedule_out(C.Structure):
+    _fields_ = [(n, _vp) for n in (
+        "bound", "status", "n_groups", "n_seg", "n_rows", "n_extra", "level", "wanc", "block_of",
+        "group_of", "exec_group", "m", "group_R", "seg_parent", "seg_load", "seg_m", "seg_group",
+        "row_id", "row_group", "row_m0", "row_load", "extra_off", "extra_src", "extra_dst")]
+
+
+def _sig(name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+dagrt_create = _sig("dagrt_create", C.c_int, [C.POINTER(_vp), C.c_int, _vp])
+dagrt_set_stream = _sig("dagrt_set_stream", C.c_int, [_vp, _vp])
+dagrt_sync = _sig("dagrt_sync", C.c_int, [_vp])
+dagrt_destroy = _sig("dagrt_destroy", None, [_vp])
+dagrt_last_error = _sig("dagrt_last_error", C.c_char_p, [_vp])
+dagrt_load_csr = _sig("dagrt_load_csr", C.c_int,
+                      [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_uint32, C.POINTER(_vp)])
+dagrt_batch_free = _sig("dagrt_batch_free", None, [_vp])
+dagrt_batch_n_dags = _sig("dagrt_batch_n_dags", C.c_int32, [_vp])
+dagrt_batch_total_nodes = _sig("dagrt_batch_total_nodes", C.c_int64, [_vp])
+dagrt_schedule = _sig("dagrt_schedule", C.c_int, [_vp, C.c_int32, C.POINTER(dagrt_schedule_out), C.c_uint32])
+dagrt_bound = _sig("dagrt_bound", C.c_int,
+                   [_vp, C.c_int32, C.POINTER(C.c_int32), C.c_int32, _vp, C.c_int64, _vp, _vp, _vp, C.c_uint32])
+
+
+class DagrtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dagrt error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(x):
+    """Address of a numpy array or a torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    return x.data_ptr()  # torch tensor
+
+
+def _is_device(x):
+    return x is not None and not isinstance(x, np.ndarray) and getattr(x, "is_cuda", False)
+
+
+# per-node / per-DAG output fields and their dtypes
+_DAG_FIELDS = {"bound": np.int64, "status": np.int32, "n_groups": np.int32, "n_seg": np.int32,
+               "n_rows": np.int32, "n_extra": np.int64}
+_NODE_FIELDS = {"level": np.int32, "wanc": np.int64, "block_of": np.int32, "group_of": np.int32,
+                "exec_group": np.int32, "m": np.int32, "group_R": np.int64, "seg_parent": np.int32,
+                "seg_load": np.int64, "seg_m": np.int32, "seg_group": np.int32}
+_ROW_FIELDS = {"row_id": np.int32, "row_group": np.int32, "row_m0": np.int32, "row_load": np.int64}
+ALL_FIELDS = tuple(_DAG_FIELDS) + tuple(_NODE_FIELDS) + tuple(_ROW_FIELDS)
+
+
+class Context:
+    def __init__(self, device: int = 0, stream=None):
+        h = _vp()
+        rc = dagrt_create(C.byref(h), int(device), stream)
+        if rc != OK:
+            raise DagrtError(rc, "dagrt_create failed (no usable CUDA device?)")
+        self.h = h
+        self.device = device
+
+    def check(self, rc):
+        if rc != OK:
+            raise DagrtError(rc, dagrt_last_error(self.h).decode())
+        return rc
+
+    def set_stream(self, stream):
+        self.check(dagrt_set_stream(self.h, stream))
+
+    def sync(self):
+        self.check(dagrt_sync(self.h))
+
+    def close(self):
+        if self.h:
+            dagrt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, arrays, M: int | None = None) -> "LoadedBatch":
+        """Load a batch: a workloads.Batch (host numpy arrays, copied) or a dict of torch
+        CUDA tensors with keys node_off, edge_off, row_ptr, col, wcet, k64 (used in place)."""
+        if isinstance(arrays, dict):
+            a = arrays
+            if M is None:
+                M = int(a["M"])
+            flags = PTR_DEVICE if _is_device(a["wcet"]) else 0
+            n = int(a["node_off"].shape[0]) - 1
+        else:
+            a = {k: np.ascontiguousarray(getattr(arrays, k)) for k in
+                 ("node_off", "edge_off", "row_ptr", "col", "wcet", "k64")}
+            M = arrays.M if M is None else M
+            flags = 0
+            n = arrays.n_dags
+        h = _vp()
+        rc = dagrt_load_csr(self.h, n, _ptr(a["node_off"]), _ptr(a["edge_off"]), _ptr(a["row_ptr"]),
+                            _ptr(a["col"]), _ptr(a["wcet"]), _ptr(a["k64"]), int(M), flags, C.byref(h))
+        self.check(rc)
+        return LoadedBatch(self, h, n, M, keep=a)
+
+
+class LoadedBatch:
+    def __init__(self, ctx: Context, h, n_dags: int, M: int, keep=None):
+        self.ctx, self.h, self.n_dags, self.M = ctx, h, n_dags, M
+        self._keep = keep  # device inputs must outlive the batch
+        self.total_nodes = int(dagrt_batch_total_nodes(h))
+
+    def free(self):
+        if self.h:
+            dagrt_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def schedule(self, variant: int = VAR_PAPER, fields=("bound", "status"), extra_cap=None,
+                 out=None, check: bool = True):
+        """Run the scheduler. With `out` (a dict of torch CUDA tensors) the call enqueues
+        device work only and returns `out`; otherwise the requested fields come back as
+        numpy arrays. extra_cap: per-DAG capacities of the extra-edge buffer (host)."""
+        o = dagrt_schedule_out()
+        if out is not None:
+            for k, t in out.items():
+                setattr(o, k, _ptr(t))
+            rc = dagrt_schedule(self.h, int(variant), C.byref(o), PTR_DEVICE)
+            if check:
+                self.ctx.check(rc)
+            return out
+        res = {}
+        nd, nn = self.n_dags, self.total_nodes
+        for f in fields:
+            if f in _DAG_FIELDS:
+                res[f] = np.zeros(max(nd, 1), _DAG_FIELDS[f])
+            elif f in _NODE_FIELDS:
+                res[f] = np.zeros(max(nn, 1), _NODE_FIELDS[f])
+            elif f in _ROW_FIELDS:
+                res[f] = np.zeros(max(2 * nn, 1), _ROW_FIELDS[f])
+            else:
+                raise KeyError(f)
+            setattr(o, f, _ptr(res[f]))
+        if extra_cap is not None:
+            cap = np.asarray(extra_cap, np.int64)
+            eo = np.zeros(nd + 1, np.int64)
+            eo[1:] = np.cumsum(cap)
+            res["extra_off"] = eo
+            res["extra_src"] = np.zeros(max(int(eo[-1]), 1), np.int32)
+            res["extra_dst"] = np.zeros(max(int(eo[-1]), 1), np.int32)
+            for f in ("extra_off", "extra_src", "extra_dst"):
+                setattr(o, f, _ptr(res[f]))
+        rc = dagrt_schedule(self.h, int(variant), C.byref(o), 0)
+        res["rc"] = rc
+        if check and rc not in (OK, E_INVAL, E_RANGE, E_CYCLE, E_CAP):
+            self.ctx.check(rc)
+        for f in list(res):
+            if f in _DAG_FIELDS:
+                res[f] = res[f][:nd]
+        return res
+
+    def bound(self, variant_ids, n_alloc: int, m_alloc, cand_stride: int, out_bound=None,
+              best_bound=None, best_cand=None, want_all: bool = True):
+        """Bounds of candidate allocations (see dagrt_bound). Host numpy inputs return
+        numpy outputs; torch CUDA inputs need torch CUDA outputs and only enqueue."""
+        vids = (C.c_int32 * len(variant_ids))(*[int(v) for v in variant_ids])
+        n_cand = len(variant_ids) * n_alloc
+        if _is_device(m_alloc):
+            rc = dagrt_bound(self.h, len(variant_ids), vids, int(n_alloc), _ptr(m_alloc), int(cand_stride),
+                             _ptr(out_bound), _ptr(best_bound), _ptr(best_cand), PTR_DEVICE)
+            self.ctx.check(rc)
+            return out_bound, best_bound, best_cand
+        m_alloc = np.ascontiguousarray(m_alloc, np.uint8)
+        ob = np.zeros(max(self.n_dags * n_cand, 1), np.int64) if want_all else None
+        bb = np.zeros(max(self.n_dags, 1), np.int64)
+        bc = np.zeros(max(self.n_dags, 1), np.int32)
+        rc = dagrt_bound(self.h, len(variant_ids), vids, int(n_alloc), _ptr(m_alloc), int(cand_stride),
+                         _ptr(ob), _ptr(bb), _ptr(bc), 0)
+        self.ctx.check(rc)
+        return (ob[:self.n_dags * n_cand].reshape(self.n_dags, n_cand) if want_all else None,
+                bb[:self.n_dags], bc[:self.n_dags])

@@ -1,0 +1,89 @@
+"""GPU parity of candidate-allocation bounds and the argmin against the CPU oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_20826_gb300 import workloads as wl
+from tests.gpu_helpers import context
+from tests.oracle_checks import random_small_dag
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    return context()
+
+
+def _run(ctx, batch, variants, n_alloc, alloc, stride, dags=None):
+    lb = ctx.load(batch)
+    for v in sorted(set(variants)):
+        lb.schedule(v, fields=("status",))
+    ob, bb, bc = lb.bound(variants, n_alloc, alloc, stride)
+    for d in (range(batch.n_dags) if dags is None else dags):
+        ref, rb, rc = oracle.search_dag(batch, d, alloc, stride, len(variants), n_alloc, variants)
+        assert np.array_equal(ob[d], ref), (d, np.nonzero(ob[d] != ref)[0][:5])
+        assert bb[d] == rb and bc[d] == rc, (d, bb[d], rb, bc[d], rc)
+    lb.free()
+    return ob, bb, bc
+
+
+def test_config1_full(ctx):
+    """One 20-node DAG, M = 8: the paper's own allocation plus 4,096 random ones from
+    {1, 2, 4, 8}."""
+    b = wl.config(1)
+    alloc, stride = wl.candidate_allocations(b, 1, 4097, [1, 2, 4, 8], seed=wl.BASE_SEED + 11)
+    ob, bb, bc = _run(ctx, b, [0], 4097, alloc, stride)
+    rc, ref = oracle.schedule_dag_of(b, 0)
+    assert ob[0, 0] == ref["bound"]  # candidate 0 keeps the scheduled allocation
+
+
+def test_config3_sampled_all_variants(ctx):
+    b = wl.config(3, n_dags=60)
+    alloc, stride = wl.candidate_allocations(b, 4, 64, [1, 2, 4, 8, 16, 32], seed=wl.BASE_SEED + 13)
+    _run(ctx, b, [0, 1, 2, 3], 64, alloc, stride)
+
+
+def test_arbitrary_allocations_and_M(ctx):
+    """Any byte value (non powers of two, above M) exercises every division path."""
+    rng = np.random.default_rng(17)
+    for M in (1, 3, 8, 100, 148, 4096):
+        dags = [random_small_dag(rng, int(rng.integers(1, 60)), 0.15, int(rng.choice([10, 10**4, 2**32 - 1])))
+                for _ in range(30)]
+        b = wl.from_dags(dags, M)
+        alloc, stride = wl.candidate_allocations(b, 2, 40, list(range(0, 256)), seed=M, keep_scheduled=True)
+        _run(ctx, b, [0, 3], 40, alloc, stride)
+
+
+def test_device_path_and_stride(ctx):
+    import torch
+    b = wl.small_config(3, n_dags=50, v_lo=20, v_hi=300)
+    alloc, stride = wl.candidate_allocations(b, 2, 24, [1, 2, 4, 8, 16, 32], seed=5, cand_stride=64)
+    lb = ctx.load(b)
+    lb.schedule(0, fields=("status",))
+    lb.schedule(2, fields=("status",))
+    ob_h, bb_h, bc_h = lb.bound([0, 2], 24, alloc, stride)
+    da = torch.from_numpy(alloc).cuda()
+    ob = torch.zeros(b.n_dags * 48, dtype=torch.int64, device="cuda")
+    bb = torch.zeros(b.n_dags, dtype=torch.int64, device="cuda")
+    bc = torch.zeros(b.n_dags, dtype=torch.int32, device="cuda")
+    lb.bound([0, 2], 24, da, stride, ob, bb, bc)
+    torch.cuda.synchronize()
+    assert np.array_equal(ob.cpu().numpy().reshape(b.n_dags, 48), ob_h)
+    assert np.array_equal(bb.cpu().numpy(), bb_h) and np.array_equal(bc.cpu().numpy(), bc_h)
+    for d in range(0, b.n_dags, 7):
+        ref, rb, rc = oracle.search_dag(b, d, alloc, stride, 2, 24, [0, 2])
+        assert np.array_equal(ob_h[d], ref)
+
+
+def test_unscheduled_variant_is_rejected(ctx):
+    from paper_2602_20826_gb300.dagrt import DagrtError
+    b = wl.small_config(2, n_dags=4, v_lo=5, v_hi=20)
+    alloc, stride = wl.candidate_allocations(b, 1, 4, [1, 2], seed=1)
+    lb = ctx.load(b)
+    with pytest.raises(DagrtError):
+        lb.bound([1], 4, alloc, stride)
