@@ -86,6 +86,9 @@ void dagrt_destroy(dagrt_ctx *ctx);
 /* Text of the last error on this context ("" if none). Valid until the next call. */
 const char *dagrt_last_error(const dagrt_ctx *ctx);
 
+/* Number of kernels this context has launched so far (all calls), or -1 for NULL. */
+int64_t dagrt_launch_count(const dagrt_ctx *ctx);
+
 /* Load a batch of n_dags DAGs (System Model, Sec. 2.1: G = (V, E), C^_i; plus the
  * parallel fraction k_i/64 of each kernel) for an M-SM GPU (Sec. 2).
  *   node_off[n_dags+1] int64  DAG d owns nodes node_off[d] .. node_off[d+1]-1

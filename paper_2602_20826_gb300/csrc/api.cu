@@ -4,6 +4,7 @@
 // classes of DAGs for the scheduling kernels, and host<->device marshalling of outputs.
 #include <algorithm>
 #include <cstdarg>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -15,12 +16,39 @@
 
 using namespace dagrt;
 
+// Device buffers are recycled through a per-context pool (exact-size free lists), so a
+// batch that is loaded and freed every step allocates nothing after the first step.
+struct DevicePool {
+    std::multimap<size_t, void *> free_list;
+    std::vector<void *> all;
+    cudaError_t get(void **p, size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        auto it = free_list.find(bytes);
+        if (it != free_list.end()) {
+            *p = it->second;
+            free_list.erase(it);
+            return cudaSuccess;
+        }
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) all.push_back(*p);
+        return e;
+    }
+    void put(void *p, size_t bytes) { free_list.emplace((bytes + 255) / 256 * 256, p); }
+    void release_all() {
+        for (void *p : all) cudaFree(p);
+        all.clear();
+        free_list.clear();
+    }
+};
+
 struct dagrt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int n_sm = 0;
     std::string err;
     int n_batches = 0;
+    int64_t launches = 0;
+    DevicePool pool;
 };
 
 namespace {
@@ -47,7 +75,7 @@ struct dagrt_batch {
     const int64_t *node_off = nullptr, *edge_off = nullptr, *wcet = nullptr;
     const int32_t *row_ptr = nullptr, *col = nullptr;
     const uint8_t *k64 = nullptr;
-    std::vector<void *> owned;  // device allocations freed with the batch
+    std::vector<std::pair<void *, size_t>> owned;  // pooled device buffers of the batch
     std::vector<int64_t> h_node_off;
     // size classes: warp classes then the CTA class, lists concatenated
     int32_t *lists = nullptr;
@@ -89,9 +117,21 @@ template <class T>
 static cudaError_t batch_alloc(dagrt_batch *b, T **p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
-    if (e == cudaSuccess) b->owned.push_back((void *)*p);
+    void *q = nullptr;
+    cudaError_t e = b->ctx->pool.get(&q, n * sizeof(T));
+    if (e == cudaSuccess) {
+        *p = (T *)q;
+        b->owned.emplace_back(q, n * sizeof(T));
+    }
     return e;
+}
+
+static void batch_release(dagrt_batch *b) {
+    for (auto &pb : b->owned) b->ctx->pool.put(pb.first, pb.second);
+    b->owned.clear();
+    if (b->tmp) b->ctx->pool.put(b->tmp, b->tmp_cap);
+    b->tmp = nullptr;
+    b->tmp_cap = 0;
 }
 
 extern "C" {
@@ -128,10 +168,15 @@ int dagrt_sync(dagrt_ctx *ctx) {
 
 void dagrt_destroy(dagrt_ctx *ctx) {
     if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->pool.release_all();
     delete ctx;
 }
 
 const char *dagrt_last_error(const dagrt_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t dagrt_launch_count(const dagrt_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
 int32_t dagrt_batch_n_dags(const dagrt_batch *b) { return b ? b->n_dags : -1; }
 int64_t dagrt_batch_total_nodes(const dagrt_batch *b) { return b ? b->total_nodes : -1; }
@@ -140,8 +185,7 @@ void dagrt_batch_free(dagrt_batch *b) {
     if (!b) return;
     cudaSetDevice(b->ctx->device);
     cudaStreamSynchronize(b->ctx->stream);
-    for (void *p : b->owned) cudaFree(p);
-    if (b->tmp) cudaFree(b->tmp);
+    batch_release(b);
     b->ctx->n_batches--;
     delete b;
 }
@@ -191,7 +235,7 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
     b->max_v = max_v;
     b->h_node_off = hn;
     auto bail = [&](int code) {
-        for (void *p : b->owned) cudaFree(p);
+        batch_release(b);
         delete b;
         return code;
     };
@@ -232,10 +276,10 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
     {
         std::vector<std::vector<int32_t>> cls(kNumWarpClasses + 1);
         std::vector<int32_t> order(n_dags);
-        std::vector<int32_t> cnt(DAGRT_MAX_V + 2, 0);
-        for (int d = 0; d < n_dags; d++) cnt[DAGRT_MAX_V - (int)(hn[d + 1] - hn[d])]++;
+        std::vector<int32_t> cnt(max_v + 2, 0);  // counting sort by descending V
+        for (int d = 0; d < n_dags; d++) cnt[max_v - (int)(hn[d + 1] - hn[d])]++;
         for (int i = 1; i < (int)cnt.size(); i++) cnt[i] += cnt[i - 1];
-        for (int d = n_dags - 1; d >= 0; d--) order[--cnt[DAGRT_MAX_V - (int)(hn[d + 1] - hn[d])]] = d;
+        for (int d = n_dags - 1; d >= 0; d--) order[--cnt[max_v - (int)(hn[d + 1] - hn[d])]] = d;
         int big_v = 0;
         for (int d : order) {
             const int v = (int)(hn[d + 1] - hn[d]);
@@ -306,10 +350,11 @@ static int ensure_tmp(dagrt_batch *b, size_t bytes) {
     dagrt_ctx *ctx = b->ctx;
     if (b->tmp_cap >= bytes) return DAGRT_OK;
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
-    if (b->tmp) cudaFree(b->tmp);
+    if (b->tmp) ctx->pool.put(b->tmp, b->tmp_cap);
     b->tmp = nullptr;
     b->tmp_cap = 0;
-    CK(cudaMalloc(&b->tmp, bytes), "allocate scratch");
+    bytes = (bytes + 255) / 256 * 256;
+    CK(ctx->pool.get(&b->tmp, bytes), "allocate scratch");
     b->tmp_cap = bytes;
     return DAGRT_OK;
 }
@@ -404,6 +449,7 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
             a.n_list = n;
             a.counter = b->counters + c;
             CK(sched_launch_warp(kWarpClassCap[c], a, ctx->n_sm, ctx->stream), "launch scheduler (warp teams)");
+            ctx->launches++;
         }
         const int nbig = b->class_off[kNumWarpClasses + 1] - b->class_off[kNumWarpClasses];
         if (nbig > 0) {
@@ -414,6 +460,7 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
             a.gws_stride = b->gws_stride;
             a.vcap = b->big_vcap;
             CK(sched_launch_cta(a, b->big_grid, ctx->stream), "launch scheduler (CTA teams)");
+            ctx->launches++;
         }
     }
     p.valid = true;
@@ -495,6 +542,7 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
         a.best_cand = best_cand ? d_bc : nullptr;
     }
     CK(bound_launch(a, ctx->n_sm, ctx->stream), "launch bound kernel");
+    ctx->launches += (a.best_bound || a.best_cand) ? 2 : 1;
     if (dev) return DAGRT_OK;
     if (out_bound && out_bytes) CK(cudaMemcpyAsync(out_bound, d_out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy bounds");
     if (best_bound && nd) CK(cudaMemcpyAsync(best_bound, d_bb, 8 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy best");

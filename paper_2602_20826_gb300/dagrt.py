@@ -50,6 +50,7 @@ dagrt_set_stream = _sig("dagrt_set_stream", C.c_int, [_vp, _vp])
 dagrt_sync = _sig("dagrt_sync", C.c_int, [_vp])
 dagrt_destroy = _sig("dagrt_destroy", None, [_vp])
 dagrt_last_error = _sig("dagrt_last_error", C.c_char_p, [_vp])
+dagrt_launch_count = _sig("dagrt_launch_count", C.c_int64, [_vp])
 dagrt_load_csr = _sig("dagrt_load_csr", C.c_int,
                       [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_uint32, C.POINTER(_vp)])
 dagrt_batch_free = _sig("dagrt_batch_free", None, [_vp])
@@ -109,6 +110,9 @@ class Context:
 
     def sync(self):
         self.check(dagrt_sync(self.h))
+
+    def launches(self) -> int:
+        return int(dagrt_launch_count(self.h))
 
     def close(self):
         if self.h:
