@@ -43,7 +43,7 @@ extern "C" {
                                  that is not strictly increasing (duplicates included) */
 #define DAGRT_E_OOM (-4)      /* device or pinned-host allocation failed */
 #define DAGRT_E_DEVICE (-5)   /* a CUDA call failed */
-#define DAGRT_E_TIMEOUT (-6)  /* reserved: a bounded device loop gave up */
+#define DAGRT_E_TIMEOUT (-6)  /* a bounded device wait gave up (a tile copy never landed) */
 #define DAGRT_E_CAP (-7)      /* an output buffer was smaller than the result (counts are
                                  still written) */
 #define DAGRT_E_INTERNAL (-8) /* a device-side consistency check failed */
@@ -64,6 +64,7 @@ extern "C" {
 /* ---------------------------------------------------------------- limits */
 #define DAGRT_MAX_M 4096
 #define DAGRT_MAX_V 65535     /* nodes per DAG */
+#define DAGRT_MAX_E 16777216  /* edges per DAG */
 
 typedef struct dagrt_ctx dagrt_ctx;
 typedef struct dagrt_batch dagrt_batch;
@@ -94,6 +95,7 @@ int64_t dagrt_launch_count(const dagrt_ctx *ctx);
  *   node_off[n_dags+1] int64  DAG d owns nodes node_off[d] .. node_off[d+1]-1
  *                             (V_d <= DAGRT_MAX_V; V_d = 0 is an empty DAG)
  *   edge_off[n_dags+1] int64  DAG d owns edges edge_off[d] .. edge_off[d+1]-1
+ *                             (E_d <= DAGRT_MAX_E)
  *   row_ptr[total_nodes + n_dags] int32  successor CSR of DAG d: its V_d+1 entries start
  *                             at node_off[d] + d, are local to edge_off[d], start at 0,
  *                             never decrease and end at E_d
@@ -169,7 +171,9 @@ int dagrt_schedule(dagrt_batch *batch, int32_t variant, const dagrt_schedule_out
  *   m_alloc                  uint8 SMs per plan row and candidate, laid out
  *                            [(2*node_off[d] + row) * cand_stride + c]; 0 = keep the
  *                            scheduled m of the row
- *   cand_stride              >= n_variants*n_alloc and a multiple of 16
+ *   cand_stride              >= n_variants*n_alloc, <= 65536 and a multiple of 16; a
+ *                            device m_alloc must be 16-byte aligned and hold
+ *                            2*total_nodes rows
  *   out_bound                [n_dags * n_cand] int64 (may be NULL)
  *   best_bound, best_cand    [n_dags] argmin over candidates (smallest bound, then
  *                            smallest candidate id); may be NULL

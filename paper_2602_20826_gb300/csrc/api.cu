@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/dagrt.h"
+#include "dagrt.h"
 #include "bound.cuh"
 #include "sched.cuh"
 
@@ -53,14 +53,14 @@ struct dagrt_ctx {
 
 namespace {
 
-constexpr int kNumWarpClasses = 3;
-constexpr int kWarpClassCap[kNumWarpClasses] = {64, 128, 256};
+constexpr int kNumWarpClasses = 4;
+constexpr int kWarpClassCap[kNumWarpClasses] = {64, 128, 192, 256};
 
 struct Plan {
     bool valid = false;
-    uint2 *lc = nullptr;
-    uint32_t *mkf = nullptr;
+    uint4 *rows = nullptr;
     int32_t *nrows = nullptr;
+    int32_t *pflag = nullptr;
     int32_t *status = nullptr;
     int64_t *bound = nullptr;
 };
@@ -81,10 +81,11 @@ struct dagrt_batch {
     int32_t *lists = nullptr;
     int32_t *counters = nullptr;
     int class_off[kNumWarpClasses + 2] = {0};
-    int max_v = 0, big_vcap = 0, big_grid = 0;
+    int max_v = 0, big_vcap = 0, big_ecap = 0, big_grid = 0;
     unsigned char *gws = nullptr;
     int64_t gws_stride = 0;
     Plan plan[DAGRT_N_VARIANTS];
+    int32_t *err = nullptr;  // device error word (bounded waits that gave up)
     // scratch for candidate evaluation
     void *tmp = nullptr;
     size_t tmp_cap = 0;
@@ -220,6 +221,7 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
         const int64_t v = hn[d + 1] - hn[d], e = he[d + 1] - he[d];
         if (v < 0 || e < 0) return fail(ctx, DAGRT_E_INVAL, "dagrt_load_csr: offsets decrease at DAG %d", d);
         if (v > DAGRT_MAX_V) return fail(ctx, DAGRT_E_INVAL, "dagrt_load_csr: DAG %d has %lld > %d nodes", d, (long long)v, DAGRT_MAX_V);
+        if (e > DAGRT_MAX_E) return fail(ctx, DAGRT_E_INVAL, "dagrt_load_csr: DAG %d has %lld > %d edges", d, (long long)e, DAGRT_MAX_E);
         max_v = std::max<int>(max_v, (int)v);
     }
     const int64_t tn = hn[n_dags], te = he[n_dags];
@@ -281,13 +283,19 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
         for (int i = 1; i < (int)cnt.size(); i++) cnt[i] += cnt[i - 1];
         for (int d = n_dags - 1; d >= 0; d--) order[--cnt[max_v - (int)(hn[d + 1] - hn[d])]] = d;
         int big_v = 0;
+        int64_t big_e = 0;
         for (int d : order) {
             const int v = (int)(hn[d + 1] - hn[d]);
-            int c = 0;
-            while (c < kNumWarpClasses && v > kWarpClassCap[c]) c++;
+            const int64_t ed = he[d + 1] - he[d];
+            int c = 0;  // the smallest class whose workspace holds V nodes and E edges
+            while (c < kNumWarpClasses && (v > kWarpClassCap[c] || ed > (int64_t)kEdgesPerNode * kWarpClassCap[c])) c++;
             cls[c].push_back(d);
-            if (c == kNumWarpClasses) big_v = std::max(big_v, v);
+            if (c == kNumWarpClasses) {
+                big_v = std::max(big_v, v);
+                big_e = std::max(big_e, ed);
+            }
         }
+        b->big_ecap = (int)big_e;
         int off = 0;
         for (int c = 0; c <= kNumWarpClasses; c++) {
             b->class_off[c] = off;
@@ -298,7 +306,8 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
         b->big_vcap = big_v;
     }
     if ((e = batch_alloc(b, &b->lists, n_dags)) != cudaSuccess ||
-        (e = batch_alloc(b, &b->counters, 8)) != cudaSuccess)
+        (e = batch_alloc(b, &b->counters, 8)) != cudaSuccess || (e = batch_alloc(b, &b->err, 1)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->err, 0, sizeof(int32_t), ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "allocate class lists"));
     if (n_dags > 0 &&
         (e = cudaMemcpyAsync(b->lists, lists.data(), 4 * n_dags, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
@@ -306,7 +315,7 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
     const int n_big = b->class_off[kNumWarpClasses + 1] - b->class_off[kNumWarpClasses];
     if (n_big > 0) {
         b->big_grid = std::min(sched_cta_grid(ctx->n_sm), n_big);
-        b->gws_stride = sched_ws_bytes(b->big_vcap);
+        b->gws_stride = sched_ws_bytes(b->big_vcap, b->big_ecap);
         unsigned char *g;
         if ((e = batch_alloc(b, &g, (size_t)b->gws_stride * b->big_grid)) != cudaSuccess)
             return bail(cuda_fail(ctx, e, "allocate large-DAG workspace"));
@@ -335,11 +344,12 @@ struct OutField {
 static int ensure_plan(dagrt_batch *b, int variant) {
     dagrt_ctx *ctx = b->ctx;
     Plan &p = b->plan[variant];
-    if (p.lc) return DAGRT_OK;
+    if (p.rows) return DAGRT_OK;
     cudaError_t e;
     const size_t rows = (size_t)(2 * b->total_nodes);
-    if ((e = batch_alloc(b, &p.lc, rows)) != cudaSuccess || (e = batch_alloc(b, &p.mkf, rows)) != cudaSuccess ||
+    if ((e = batch_alloc(b, &p.rows, rows)) != cudaSuccess ||
         (e = batch_alloc(b, &p.nrows, b->n_dags)) != cudaSuccess ||
+        (e = batch_alloc(b, &p.pflag, b->n_dags)) != cudaSuccess ||
         (e = batch_alloc(b, &p.status, b->n_dags)) != cudaSuccess ||
         (e = batch_alloc(b, &p.bound, b->n_dags)) != cudaSuccess)
         return cuda_fail(ctx, e, "allocate plan");
@@ -437,8 +447,8 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
     a.status = p.status;
     a.bound = p.bound;
     a.nrows = p.nrows;
-    a.plan_lc = p.lc;
-    a.plan_mkf = p.mkf;
+    a.pflag = p.pflag;
+    a.plan = p.rows;
     a.o = dv;
     if (nd > 0) {
         CK(cudaMemsetAsync(b->counters, 0, 8 * sizeof(int32_t), ctx->stream), "reset counters");
@@ -459,6 +469,7 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
             a.gws = b->gws;
             a.gws_stride = b->gws_stride;
             a.vcap = b->big_vcap;
+            a.ecap = b->big_ecap;
             CK(sched_launch_cta(a, b->big_grid, ctx->stream), "launch scheduler (CTA teams)");
             ctx->launches++;
         }
@@ -491,8 +502,8 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
     if (n_alloc < 1) return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: n_alloc < 1");
     const int64_t n_cand = (int64_t)n_variants * n_alloc;
     if (n_cand > (1ll << 30)) return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: too many candidates");
-    if (cand_stride < n_cand || cand_stride % 16 != 0)
-        return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: cand_stride must be >= n_cand and a multiple of 16");
+    if (cand_stride < n_cand || cand_stride % 16 != 0 || cand_stride > 65536)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: cand_stride must be >= n_cand, <= 65536 and a multiple of 16");
     if (!m_alloc && b->total_nodes > 0) return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: m_alloc is NULL");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     BoundArgs a;
@@ -503,37 +514,43 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
     a.n_variants = n_variants;
     a.n_alloc = n_alloc;
     a.stride = cand_stride;
+    a.err = b->err;
     for (int i = 0; i < n_variants; i++) {
         const int v = variant_ids[i];  // variant_ids is always a host array
         if (v < 0 || v >= DAGRT_N_VARIANTS || !b->plan[v].valid)
             return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: variant %d was not scheduled on this batch", v);
-        a.lc[i] = b->plan[v].lc;
-        a.mkf[i] = b->plan[v].mkf;
+        a.plan[i] = b->plan[v].rows;
         a.nrows[i] = b->plan[v].nrows;
+        a.pflag[i] = b->plan[v].pflag;
         a.status[i] = b->plan[v].status;
     }
     const bool dev = (flags & DAGRT_PTR_DEVICE) != 0;
     const size_t nd = b->n_dags;
     const size_t alloc_bytes = (size_t)(2 * b->total_nodes) * (size_t)cand_stride;
     const size_t out_bytes = nd * (size_t)n_cand * 8;
-    size_t need = out_bytes + 256 + 16 * nd + 256;
-    if (!dev) need += alloc_bytes + 256;
-    int rc = ensure_tmp(b, need);
-    if (rc) return rc;
-    char *t = (char *)b->tmp;
-    int64_t *d_out = (int64_t *)t;
-    t += (out_bytes + 255) / 256 * 256;
-    int64_t *d_bb = (int64_t *)t;
-    t += (8 * nd + 255) / 256 * 256;
-    int32_t *d_bc = (int32_t *)t;
-    t += (4 * nd + 255) / 256 * 256;
     if (dev) {
+        if ((uintptr_t)m_alloc % 16 != 0)
+            return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: device m_alloc must be 16-byte aligned");
         a.m_alloc = m_alloc;
-        a.out = out_bound ? out_bound : d_out;
+        a.out = out_bound;
         a.best_bound = best_bound;
         a.best_cand = best_cand;
-    } else {
+    } else {  // stage through one device scratch block
+        const size_t need = (alloc_bytes + 255) / 256 * 256 + (out_bound ? (out_bytes + 255) / 256 * 256 : 0) +
+                            (8 * nd + 255) / 256 * 256 + (4 * nd + 255) / 256 * 256 + 256;
+        int rc = ensure_tmp(b, need);
+        if (rc) return rc;
+        char *t = (char *)b->tmp;
         uint8_t *d_alloc = (uint8_t *)t;
+        t += (alloc_bytes + 255) / 256 * 256;
+        int64_t *d_out = nullptr;
+        if (out_bound) {
+            d_out = (int64_t *)t;
+            t += (out_bytes + 255) / 256 * 256;
+        }
+        int64_t *d_bb = (int64_t *)t;
+        t += (8 * nd + 255) / 256 * 256;
+        int32_t *d_bc = (int32_t *)t;
         if (alloc_bytes)
             CK(cudaMemcpyAsync(d_alloc, m_alloc, alloc_bytes, cudaMemcpyHostToDevice, ctx->stream), "copy m_alloc");
         a.m_alloc = d_alloc;
@@ -542,11 +559,14 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
         a.best_cand = best_cand ? d_bc : nullptr;
     }
     CK(bound_launch(a, ctx->n_sm, ctx->stream), "launch bound kernel");
-    ctx->launches += (a.best_bound || a.best_cand) ? 2 : 1;
+    if (nd) ctx->launches++;
     if (dev) return DAGRT_OK;
-    if (out_bound && out_bytes) CK(cudaMemcpyAsync(out_bound, d_out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy bounds");
-    if (best_bound && nd) CK(cudaMemcpyAsync(best_bound, d_bb, 8 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy best");
-    if (best_cand && nd) CK(cudaMemcpyAsync(best_cand, d_bc, 4 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy best");
+    if (out_bound && out_bytes) CK(cudaMemcpyAsync(out_bound, a.out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy bounds");
+    if (best_bound && nd) CK(cudaMemcpyAsync(best_bound, a.best_bound, 8 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy best");
+    if (best_cand && nd) CK(cudaMemcpyAsync(best_cand, a.best_cand, 4 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy best");
+    int32_t err = 0;
+    CK(cudaMemcpyAsync(&err, b->err, sizeof err, cudaMemcpyDeviceToHost, ctx->stream), "copy error word");
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    if (err) return fail(ctx, err, "dagrt_bound: a tile copy did not complete in time");
     return DAGRT_OK;
 }

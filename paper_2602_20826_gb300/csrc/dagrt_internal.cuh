@@ -9,7 +9,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/dagrt.h"
+#include "dagrt.h"
 
 namespace dagrt {
 
@@ -169,14 +169,18 @@ __device__ __forceinline__ uint64_t exec_time(uint64_t x, uint32_t k, uint32_t m
 
 // Largest load p in [1, L-1] that finishes within R ticks on min(p, S) SMs (S <= M):
 // closed form of the node-segmentation size (see the scheduler for the derivation).
+__device__ __forceinline__ uint64_t udiv(uint64_t n, uint64_t d) {  // 32-bit divide when both fit
+    return (n >> 32) == 0 && (d >> 32) == 0 ? (uint64_t)((uint32_t)n / (uint32_t)d) : n / d;
+}
+
 __device__ __forceinline__ uint64_t split_size(uint64_t L, uint32_t k, uint32_t S, uint64_t R) {
     uint64_t a = 64ull * S - (uint64_t)k * (S - 1);
-    uint64_t x2 = (64ull * S * R) / a;          // largest x >= S with x*a <= 64*S*R
+    uint64_t x2 = udiv(64ull * S * R, a);       // largest x >= S with x*a <= 64*S*R
     uint64_t p;
     if (x2 >= S) {
         p = x2;
     } else {                                    // k < 64 here; the answer is below S
-        uint64_t x1 = (64ull * R - k) / (64ull - k);
+        uint64_t x1 = udiv(64ull * R - k, 64ull - k);
         p = x1 < (uint64_t)S - 1 ? x1 : (uint64_t)S - 1;
     }
     if (p > L - 1) p = L - 1;

@@ -6,29 +6,49 @@
 // (Eq.2), Theta and the blocks of Eq.3, the balanced groups of Alg.1, the scheduling loop
 // of Alg.2 and the bound of Theorem 1. The schedule is written out as "plan rows" that the
 // candidate-bound kernel evaluates other allocations on.
+//
+// Alg.2 is sequential over the groups of a DAG. Groups with few members (the common case)
+// are scheduled by one thread of the team with plain loads and stores and no team-wide
+// barrier; large groups use the whole team.
 #include "dagrt_internal.cuh"
 #include "sched.cuh"
 
 namespace dagrt {
 
 // node state bits
-enum : uint8_t { ST_ACTIVE = 1, ST_INT = 2, ST_SEL = 4, ST_DONE = 8, ST_LAUNCH = 16 };
+enum : uint8_t { ST_ACTIVE = 1, ST_INT = 2, ST_SEL = 4, ST_DONE = 8, ST_LAUNCH = 16, ST_JOIN = 32 };
+constexpr uint16_t NONE16 = 0xffff;
 
 // ------------------------------------------------------------------ workspace layout
+// Persistent arrays live for the whole DAG; the region after them is overlaid by the
+// arrays of one phase at a time (A closure, B ordering, C peeling, D member lists, E Alg.2).
 struct Ws {
-    uint32_t *load, *rem;
+    // persistent
+    uint32_t *load;
     uint8_t *kk, *st;
-    int32_t *indeg, *cnt, *lvl_off, *blk, *group_of, *gstart, *lst, *tmp;
-    uint16_t *topo, *rank, *byrank, *rnd, *gmem, *mm;
-    uint64_t *wanc, *relmask;
+    int32_t *cnt;  // atomic counters: in-degree, Kahn count, in-block parents, open preds
+    uint32_t *srp;  // the DAG's successor CSR, staged: offsets ...
+    uint16_t *scol; // ... and successor ids
+    uint16_t *indeg, *lvl_off, *topo, *rank, *byrank, *blk, *group_of, *gstart, *gmem;
+    uint64_t *relmask;
     int32_t *sc;
-    // phase-local region (reused): closure / sort / peel / member lists
-    uint64_t *anc, *planes;          // phase A
-    uint64_t *skey, *bk;             // phase B
-    int32_t *fcnt, *nround;          // phase C
-    uint64_t *bigk;                  // phase C
-    uint16_t *gtmp;                  // phase D
-    int32_t *gfill;                  // phase D
+    // phase A (+ wanc, kept through phase B)
+    uint64_t *wanc, *anc, *planes;
+    // phase B
+    uint64_t *skey;
+    uint16_t *bk, *pos;
+    int32_t *jcnt, *rs, *re;
+    // phase C
+    int32_t *fcnt, *nround;
+    uint64_t *bigk;
+    uint16_t *rnd;
+    // phase D
+    uint16_t *gtmp;
+    int32_t *gfill;
+    // phase E
+    uint32_t *rem, *cfull;
+    uint16_t *mm;
+    int32_t *lst, *tmp;
 };
 
 __host__ __device__ inline int pow2_ceil(int v) {
@@ -37,8 +57,9 @@ __host__ __device__ inline int pow2_ceil(int v) {
     return p;
 }
 
-// Carve a workspace for DAGs of up to vc nodes out of `base`; returns the bytes used.
-__host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, Ws *ws) {
+// Carve a workspace for DAGs of up to vc nodes and ec edges out of `base`; returns the
+// bytes used.
+__host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec, Ws *ws) {
     const int W = ceil_div(vc, 64) > 0 ? ceil_div(vc, 64) : 1;
     const int P = pow2_ceil(vc > 0 ? vc : 1);
     int64_t off = 0;
@@ -49,57 +70,79 @@ __host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, Ws *ws)
     };
     Ws w;
     w.load = (uint32_t *)take(4ll * vc);
-    w.rem = (uint32_t *)take(4ll * vc);
     w.kk = (uint8_t *)take(vc);
     w.st = (uint8_t *)take(vc);
-    w.indeg = (int32_t *)take(4ll * vc);
     w.cnt = (int32_t *)take(4ll * vc);
-    w.lvl_off = (int32_t *)take(4ll * (vc + 1));
-    w.blk = (int32_t *)take(4ll * vc);
-    w.group_of = (int32_t *)take(4ll * vc);
-    w.gstart = (int32_t *)take(4ll * (vc + 2));
-    w.lst = (int32_t *)take(4ll * (vc + 1));
-    w.tmp = (int32_t *)take(4ll * vc);
+    w.srp = (uint32_t *)take(4ll * (vc + 1));
+    w.scol = (uint16_t *)take(2ll * (ec > 0 ? ec : 1));
+    w.indeg = (uint16_t *)take(2ll * vc);
+    w.lvl_off = (uint16_t *)take(2ll * (vc + 1));
     w.topo = (uint16_t *)take(2ll * vc);
     w.rank = (uint16_t *)take(2ll * vc);
     w.byrank = (uint16_t *)take(2ll * vc);
-    w.rnd = (uint16_t *)take(2ll * vc);
+    w.blk = (uint16_t *)take(2ll * vc);
+    w.group_of = (uint16_t *)take(2ll * vc);
+    w.gstart = (uint16_t *)take(2ll * (vc + 2));
     w.gmem = (uint16_t *)take(2ll * vc);
-    w.mm = (uint16_t *)take(2ll * vc);
-    w.wanc = (uint64_t *)take(8ll * vc);
     w.relmask = (uint64_t *)take(8ll * W);
     w.sc = (int32_t *)take(4 * 16);
-    const int64_t xbase = off;
-    // phase A
-    int64_t xa = 0, xb = 0, xc = 0, xd = 0;
-    off = xbase;
+    const int64_t x0 = off;
+    int64_t end = off;
+    auto mark = [&]() { end = off > end ? off : end; };
+    w.wanc = (uint64_t *)take(8ll * vc);
+    const int64_t xa = off;  // phases A and B keep wanc
     w.anc = (uint64_t *)take(8ll * vc * W);
     w.planes = (uint64_t *)take(8ll * 32 * W);
-    xa = off;
-    off = xbase;
+    mark();
+    off = xa;
     w.skey = (uint64_t *)take(8ll * P);
-    w.bk = (uint64_t *)take(8ll * vc);
-    xb = off;
-    off = xbase;
+    w.bk = (uint16_t *)take(2ll * vc);
+    w.pos = (uint16_t *)take(2ll * vc);
+    w.jcnt = (int32_t *)take(4ll * vc);
+    w.rs = (int32_t *)take(4ll * vc);
+    w.re = (int32_t *)take(4ll * vc);
+    mark();
+    off = x0;
     w.fcnt = (int32_t *)take(4ll * (vc + 1));
     w.nround = (int32_t *)take(4ll * (vc + 1));
     w.bigk = (uint64_t *)take(8ll * (vc + 1));
-    xc = off;
-    off = xbase;
+    w.rnd = (uint16_t *)take(2ll * vc);
+    mark();
+    off = x0;
     w.gtmp = (uint16_t *)take(2ll * vc);
     w.gfill = (int32_t *)take(4ll * (vc + 1));
-    xd = off;
-    int64_t end = xa;
-    if (xb > end) end = xb;
-    if (xc > end) end = xc;
-    if (xd > end) end = xd;
+    mark();
+    off = x0;
+    w.rem = (uint32_t *)take(4ll * vc);
+    w.cfull = (uint32_t *)take(4ll * vc);
+    w.mm = (uint16_t *)take(2ll * vc);
+    w.lst = (int32_t *)take(4ll * (vc + 1));
+    w.tmp = (int32_t *)take(4ll * vc);
+    mark();
     if (ws) *ws = w;
     return align_up(end, 128);
 }
 
-int64_t sched_ws_bytes(int vc) { return ws_carve(nullptr, vc, nullptr); }
+int64_t sched_ws_bytes(int vc, int ec) { return ws_carve(nullptr, vc, ec, nullptr); }
 
-// ------------------------------------------------------------------ per-DAG outputs
+// ------------------------------------------------------------------ per-DAG context
+struct Dag {
+    int64_t n0, rbase, ebase, ecap;
+    int V, W, variant;
+    uint32_t M;
+    bool want_edges;
+    const uint32_t *rp;  // staged CSR
+    const uint16_t *col;
+};
+
+// Alg.2 running totals, held by the team's first thread
+struct Acc {
+    uint64_t bound;
+    int64_t nextra;
+    int nrows, nseg, nrel;  // plan rows, segments, released-and-unfinished nodes
+    bool err;
+};
+
 __device__ inline void write_failure(const SchedArgs &a, int d, int code) {
     a.status[d] = code;
     a.bound[d] = -1;
@@ -112,61 +155,394 @@ __device__ inline void write_failure(const SchedArgs &a, int d, int code) {
     if (a.o.n_extra) a.o.n_extra[d] = 0;
 }
 
-__device__ inline void write_row(const SchedArgs &a, int64_t rbase, int r, int id, int group,
-                                 uint32_t load, uint32_t k, uint32_t m, uint64_t c, bool last) {
-    const int64_t i = rbase + r;
-    a.plan_lc[i] = make_uint2(load, (uint32_t)c);
-    a.plan_mkf[i] = m | (k << 16) | ((last ? 1u : 0u) << 24);
+__device__ inline void write_row(const SchedArgs &a, const Dag &g, int r, int id, int group, uint32_t load,
+                                 uint32_t k, uint32_t m, uint64_t c) {
+    if (r >= 2 * g.V) return;
+    const int64_t i = g.rbase + r;
+    a.plan[i] = make_uint4(load, (uint32_t)c, m | (k << 16), 0u);
     if (a.o.row_id) a.o.row_id[i] = id;
     if (a.o.row_group) a.o.row_group[i] = group;
     if (a.o.row_m0) a.o.row_m0[i] = (int32_t)m;
     if (a.o.row_load) a.o.row_load[i] = load;
 }
 
+// ------------------------------------------------------------------ Alg.2 pieces
+// Launch parallel nodes for group j (Alg.2 lines 7-17): released, unfinished nodes outside
+// pi_j in descending W^anc order (lowest rank first). One thread. Returns the number of
+// launched parts (ids in ws.lst; a segment id is >= V) and of whole-node launches.
+__device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, int j, uint64_t R, uint32_t S0,
+                                Acc &acc, int *nl_out, int *nwhole_out) {
+    int nl = 0, nwhole = 0;
+    const uint32_t M = g.M;
+    if (g.variant != DAGRT_VAR_NOPARA) {
+        uint32_t S = S0;
+        uint64_t WS = R * (uint64_t)S0;  // Eq.6
+        bool stop = false;
+        for (int w = 0; w < g.W && !stop; w++) {
+            uint64_t bits = ws.relmask[w];
+            while (bits) {
+                const int b = __ffsll((long long)bits) - 1;
+                bits &= bits - 1;
+                const int u = ws.byrank[w * 64 + b];
+                if (ws.group_of[u] == j) continue;  // a member of pi_j
+                const uint32_t load = ws.rem[u], k = ws.kk[u];
+                bool split = false;
+                uint32_t mu = 0;
+                uint64_t p = 0, c = 0;
+                if (g.variant == DAGRT_VAR_LITERAL) {
+                    if (WS == 0) { stop = true; break; }
+                    if (load > WS) {
+                        split = true;
+                        p = WS;
+                        mu = (uint32_t)(p < S ? p : S);
+                    } else {
+                        mu = load < S ? load : S;
+                        WS -= load;
+                        c = exec_time(load, k, mu, M);
+                    }
+                } else {
+                    if (S == 0) { stop = true; break; }
+                    mu = load < S ? load : S;
+                    // fits within R on mu <= M SMs: ceil(load (64mu - k(mu-1)) / (64mu)) <= R
+                    const uint64_t lhs = (uint64_t)load * (64ull * mu - (uint64_t)k * (mu - 1));
+                    if (lhs > 64ull * mu * R) {
+                        if (g.variant == DAGRT_VAR_NOSEG) continue;
+                        split = true;
+                        p = split_size(load, k, S, R);
+                        mu = (uint32_t)(p < S ? p : S);
+                    } else {
+                        c = exec_time(load, k, mu, M);
+                        S -= mu;
+                    }
+                }
+                if (split) {  // node segmentation: the parallel part runs now
+                    const int s = acc.nseg++;
+                    if (a.o.seg_parent) {
+                        a.o.seg_parent[g.n0 + s] = u;
+                        a.o.seg_load[g.n0 + s] = (int64_t)p;
+                        a.o.seg_m[g.n0 + s] = (int32_t)mu;
+                        a.o.seg_group[g.n0 + s] = j;
+                    }
+                    write_row(a, g, acc.nrows++, g.V + s, j, (uint32_t)p, k, mu, exec_time(p, k, mu, M));
+                    ws.rem[u] = load - (uint32_t)p;
+                    ws.lst[nl++] = g.V + s;
+                    stop = true;
+                    break;
+                }
+                ws.st[u] |= ST_LAUNCH;
+                ws.mm[u] = (uint16_t)mu;
+                write_row(a, g, acc.nrows++, u, j, load, k, mu, c);
+                ws.lst[nl++] = u;
+                nwhole++;
+            }
+        }
+    }
+    if (acc.nrows - 1 < 2 * g.V) a.plan[g.rbase + acc.nrows - 1].z |= 1u << 24;  // last row of pi_j
+    if (acc.nrows > 2 * g.V || acc.nseg > g.V) acc.err = true;
+    *nl_out = nl;
+    *nwhole_out = nwhole;
+}
+
+// Extra dependencies (Alg.2 line 14): (v_n, succ(v_R)) for every launched part and
+// (v_R, v_n) for every unlaunched parallel node, the split node's residual included. The
+// count is always kept; the edges are written when requested. One thread.
+__device__ void extra_edges(const Ws &ws, const SchedArgs &a, const Dag &g, int j, int vR, int np, int nl,
+                            int nwhole, Acc &acc) {
+    if (g.variant == DAGRT_VAR_NOPARA) return;
+    const int outdeg = g.rp[vR + 1] - g.rp[vR];
+    if (g.want_edges) {
+        int64_t idx = acc.nextra;
+        for (int i = 0; i < nl; i++)
+            for (int e = g.rp[vR]; e < g.rp[vR + 1]; e++, idx++)
+                if (idx < g.ecap) {
+                    a.o.extra_src[g.ebase + idx] = ws.lst[i];
+                    a.o.extra_dst[g.ebase + idx] = g.col[e];
+                }
+        for (int w = 0; w < g.W; w++) {
+            uint64_t bits = ws.relmask[w];
+            while (bits) {
+                const int b = __ffsll((long long)bits) - 1;
+                bits &= bits - 1;
+                const int u = ws.byrank[w * 64 + b];
+                if (ws.group_of[u] == j || (ws.st[u] & ST_LAUNCH)) continue;
+                if (idx < g.ecap) {
+                    a.o.extra_src[g.ebase + idx] = vR;
+                    a.o.extra_dst[g.ebase + idx] = u;
+                }
+                idx++;
+            }
+        }
+    }
+    acc.nextra += (int64_t)nl * outdeg + (int64_t)(acc.nrel - np - nwhole);
+}
+
+// Group j scheduled by one thread (groups with few members).
+__device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int j, Acc &acc) {
+    const uint32_t M = g.M;
+    const int gb = ws.gstart[j], ge = ws.gstart[j + 1];
+    int np = 0;
+    uint64_t Wg = 0;
+    for (int i = gb; i < ge; i++) {
+        const int v = ws.gmem[i];
+        if (!(ws.st[v] & ST_DONE)) {
+            np++;
+            Wg += ws.rem[v];
+        }
+    }
+    if (np == 0) {  // every member already ran as a parallel node: the group is dropped
+        if (a.o.group_R) a.o.group_R[g.n0 + j] = 0;
+        return;
+    }
+    // Eq.5; a single member gets round(C^ M / C^) = M, i.e. m = min(C^, M)
+    uint32_t sum_m = 0;
+    for (int i = gb; i < ge; i++) {
+        const int v = ws.gmem[i];
+        if (ws.st[v] & ST_DONE) continue;
+        const uint32_t x = ws.rem[v];
+        uint32_t m;
+        if (np == 1) {
+            m = x < M ? x : M;
+        } else {
+            const uint64_t num = 2ull * x * M + Wg, den = 2ull * Wg;
+            uint64_t r = (num >> 32) == 0 && (den >> 32) == 0 ? (uint64_t)((uint32_t)num / (uint32_t)den) : num / den;
+            if (r < 1) r = 1;
+            m = (uint32_t)(r < x ? r : x);
+        }
+        ws.mm[v] = (uint16_t)m;
+        sum_m += m;
+    }
+    while (sum_m > M) {  // keep sum m_i <= M: trim the largest m (ties: higher id)
+        int best = -1;
+        for (int i = gb; i < ge; i++) {
+            const int v = ws.gmem[i];
+            if (ws.st[v] & ST_DONE) continue;
+            if (best < 0 || ws.mm[v] >= ws.mm[best]) best = v;
+        }
+        ws.mm[best]--;
+        sum_m--;
+    }
+    // Eq.1 per member and Lemma 1: R(pi_j) = max C_i, v_R = lowest id with C_i = R; rows
+    uint64_t R = 0;
+    int vR = -1;
+    for (int i = gb; i < ge; i++) {
+        const int v = ws.gmem[i];
+        if (ws.st[v] & ST_DONE) continue;
+        const uint32_t x = ws.rem[v], m = ws.mm[v];
+        const uint64_t c = (x == ws.load[v] && m == (x < M ? x : M)) ? ws.cfull[v] : exec_time(x, ws.kk[v], m, M);
+        if (c > R) {
+            R = c;
+            vR = v;
+        }
+        write_row(a, g, acc.nrows++, v, j, x, ws.kk[v], m, c);
+    }
+    int nl, nwhole;
+    launch_parallel(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
+    extra_edges(ws, a, g, j, vR, np, nl, nwhole, acc);
+    // members and whole launches finish with pi_j and release their successors
+    for (int i = gb; i < ge + nl; i++) {
+        int v;
+        if (i < ge) {
+            v = ws.gmem[i];
+            if (ws.st[v] & ST_DONE) continue;
+        } else {
+            v = ws.lst[i - ge];
+            if (v >= g.V) continue;  // a segment: its node is not finished
+        }
+        ws.st[v] = ST_DONE;
+        ws.rem[v] = 0;
+        if (a.o.exec_group) a.o.exec_group[g.n0 + v] = j;
+        ws.relmask[ws.rank[v] >> 6] &= ~(1ull << (ws.rank[v] & 63));
+        acc.nrel--;
+        for (int e = g.rp[v]; e < g.rp[v + 1]; e++) {
+            const int s = g.col[e];
+            if (--ws.cnt[s] == 0) {
+                ws.relmask[ws.rank[s] >> 6] |= 1ull << (ws.rank[s] & 63);
+                acc.nrel++;
+            }
+        }
+    }
+    if (a.o.group_R) a.o.group_R[g.n0 + j] = (int64_t)R;
+    acc.bound += R;
+}
+
+// Group j scheduled by the whole team (groups with many members). `acc` is only valid in
+// the team's first thread; sc[8] carries acc.nrows to the others.
+template <int NT>
+__device__ void group_team(const Team<NT> &tm, const Ws &ws, const SchedArgs &a, const Dag &g, int j, Acc &acc) {
+    const uint32_t M = g.M;
+    const bool lead = tm.t == 0;
+    volatile int32_t *sc = ws.sc;
+    const int gb = ws.gstart[j], ge = ws.gstart[j + 1];
+    uint32_t cm = 0;
+    uint64_t wl = 0;
+    for (int i = gb + tm.t; i < ge; i += NT) {
+        const int v = ws.gmem[i];
+        if (!(ws.st[v] & ST_DONE)) {
+            cm++;
+            wl += ws.rem[v];
+        }
+    }
+    const uint32_t np = (uint32_t)tm.sum(cm);
+    if (np == 0) {
+        if (lead && a.o.group_R) a.o.group_R[g.n0 + j] = 0;
+        return;
+    }
+    const uint64_t Wg = tm.sum(wl);
+    uint64_t sml = 0;
+    for (int i = gb + tm.t; i < ge; i += NT) {
+        const int v = ws.gmem[i];
+        if (ws.st[v] & ST_DONE) continue;
+        const uint64_t num = 2ull * ws.rem[v] * M + Wg, den = 2ull * Wg;
+        uint64_t r = (num >> 32) == 0 && (den >> 32) == 0 ? (uint64_t)((uint32_t)num / (uint32_t)den) : num / den;
+        if (r < 1) r = 1;
+        const uint32_t m = (uint32_t)(r < ws.rem[v] ? r : ws.rem[v]);
+        ws.mm[v] = (uint16_t)m;
+        sml += m;
+    }
+    uint64_t sum_m = tm.sum(sml);
+    tm.sync();
+    while (sum_m > M) {
+        uint64_t key = 0;
+        for (int i = gb + tm.t; i < ge; i += NT) {
+            const int v = ws.gmem[i];
+            if (ws.st[v] & ST_DONE) continue;
+            const uint64_t kv = ((uint64_t)ws.mm[v] << 16) | (uint64_t)v;
+            key = kv > key ? kv : key;
+        }
+        key = tm.maxu(key);
+        if (lead) ws.mm[key & 0xffff]--;
+        sum_m--;
+        tm.sync();
+    }
+    uint64_t ckey = 0;  // (C, 0xffff - id): the max is the largest C, then the lowest id
+    for (int i = gb + tm.t; i < ge; i += NT) {
+        const int v = ws.gmem[i];
+        if (ws.st[v] & ST_DONE) continue;
+        const uint64_t c = exec_time(ws.rem[v], ws.kk[v], ws.mm[v], M);
+        const uint64_t kv = (c << 16) | (uint64_t)(0xffff - v);
+        ckey = kv > ckey ? kv : ckey;
+    }
+    ckey = tm.maxu(ckey);
+    const uint64_t R = ckey >> 16;
+    const int vR = 0xffff - (int)(ckey & 0xffff);
+    int nrows = sc[8];
+    for (int base = gb; base < ge; base += NT) {
+        const int i = base + tm.t;
+        const bool mem = i < ge && !(ws.st[ws.gmem[i]] & ST_DONE);
+        uint32_t tot;
+        const uint32_t off = tm.excl_sum(mem ? 1u : 0u, &tot);
+        if (mem) {
+            const int v = ws.gmem[i];
+            write_row(a, g, nrows + (int)off, v, j, ws.rem[v], ws.kk[v], ws.mm[v],
+                      exec_time(ws.rem[v], ws.kk[v], ws.mm[v], M));
+        }
+        nrows += (int)tot;
+    }
+    tm.sync();
+    if (lead) {
+        acc.nrows = nrows;
+        int nl, nwhole;
+        launch_parallel(ws, a, g, j, R, M - (uint32_t)sum_m, acc, &nl, &nwhole);
+        extra_edges(ws, a, g, j, vR, (int)np, nl, nwhole, acc);
+        sc[1] = nl;
+        sc[6] = 0;
+        sc[7] = 0;
+    }
+    tm.sync();
+    const int nl = sc[1];
+    for (int i = gb + tm.t; i < ge + nl; i += NT) {
+        int v;
+        if (i < ge) {
+            v = ws.gmem[i];
+            if (ws.st[v] & ST_DONE) continue;
+        } else {
+            v = ws.lst[i - ge];
+            if (v >= g.V) continue;
+        }
+        ws.st[v] = ST_DONE;
+        ws.rem[v] = 0;
+        if (a.o.exec_group) a.o.exec_group[g.n0 + v] = j;
+        atomicAnd((unsigned long long *)&ws.relmask[ws.rank[v] >> 6], ~(1ull << (ws.rank[v] & 63)));
+        ws.tmp[atomicAdd((int *)&sc[6], 1)] = v;
+    }
+    tm.sync();
+    const int nf = sc[6];
+    for (int f = 0; f < nf; f++) {
+        const int v = ws.tmp[f];
+        for (int e = g.rp[v] + tm.t; e < g.rp[v + 1]; e += NT) {
+            const int s = g.col[e];
+            if (atomicSub(&ws.cnt[s], 1) == 1) {
+                atomicOr((unsigned long long *)&ws.relmask[ws.rank[s] >> 6], 1ull << (ws.rank[s] & 63));
+                atomicAdd((int *)&sc[7], 1);
+            }
+        }
+    }
+    tm.sync();
+    if (lead) {
+        acc.nrel += sc[7] - nf;
+        if (a.o.group_R) a.o.group_R[g.n0 + j] = (int64_t)R;
+        acc.bound += R;
+    }
+}
+
 // ------------------------------------------------------------------ one DAG
 template <int NT>
-__device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &a, int d, int vc) {
+__device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &a, int d, int vc, int ec) {
     const int64_t n0 = a.node_off[d];
     const int V = (int)(a.node_off[d + 1] - n0);
     const int64_t e0 = a.edge_off[d];
     const int64_t E = a.edge_off[d + 1] - e0;
-    const int32_t *__restrict__ rp = a.row_ptr + n0 + d;
-    const int32_t *__restrict__ col = a.col + e0;
+    const int32_t *__restrict__ grp = a.row_ptr + n0 + d;
+    const int32_t *__restrict__ gcol = a.col + e0;
     const int64_t *__restrict__ wc = a.wcet + n0;
     const uint8_t *__restrict__ kp = a.k64 + n0;
     const uint32_t M = (uint32_t)a.M;
-    const int variant = a.variant;
     volatile int32_t *sc = ws.sc;
     const bool lead = tm.t == 0;
 
-    if (V > vc) {  // routed to the wrong size class: never expected
+    if (V > vc || E > ec) {  // routed to the wrong size class: never expected
         if (lead) write_failure(a, d, DAGRT_E_INTERNAL);
         return;
     }
 
-    // ---- validation: row_ptr shape, then loads and fractions, then successor ids
+    // ---- validation: row_ptr shape, then loads and fractions, then successor ids; the
+    //      CSR is staged into the workspace on the way (all later phases read the copy)
     bool bad = false;
-    if (lead) bad = rp[0] != 0 || (int64_t)rp[V] != E;
-    for (int v = tm.t; v < V; v += NT)
-        if (rp[v + 1] < rp[v]) bad = true;
+    if (lead) bad = grp[0] != 0 || (int64_t)grp[V] != E;
+    for (int v = tm.t; v <= V; v += NT) {
+        const int x = grp[v];
+        if (v < V && grp[v + 1] < x) bad = true;
+        ws.srp[v] = (uint32_t)x;
+    }
     if (tm.any(bad)) {
         if (lead) write_failure(a, d, DAGRT_E_INVAL);
         return;
     }
     bool badv = false, badc = false;
+    for (int e = tm.t; e < (int)E; e += NT) {
+        const int c = gcol[e];
+        if (c < 0 || c >= V) badc = true;
+        ws.scol[e] = (uint16_t)c;
+    }
     for (int v = tm.t; v < V; v += NT) {
         const int64_t w = wc[v];
         const uint8_t k = kp[v];
         if (w < 1 || w > 0xffffffffll || k > 64) badv = true;
         ws.load[v] = (uint32_t)w;
         ws.kk[v] = k;
-        ws.indeg[v] = 0;
-        ws.st[v] = 0;
-        int prev = -1;
-        for (int e = rp[v]; e < rp[v + 1]; e++) {
-            const int c = col[e];
-            if (c < 0 || c >= V || c == v || c <= prev) badc = true;
-            prev = c;
+        ws.cnt[v] = 0;
+    }
+    tm.sync();
+    const uint32_t *__restrict__ rp = ws.srp;
+    const uint16_t *__restrict__ col = ws.scol;
+    if (!badc) {  // self loops, unsorted or repeated successors (ids are in range here)
+        for (int v = tm.t; v < V; v += NT) {
+            int prev = -1;
+            for (int e = rp[v]; e < (int)rp[v + 1]; e++) {
+                const int c = col[e];
+                if (c == v || c <= prev) badc = true;
+                prev = c;
+            }
         }
     }
     if (tm.any(badv)) {
@@ -193,9 +569,9 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     }
     tm.sync();
 
-    // ---- in-degrees; join = at least two predecessors
+    // ---- in-degrees (a join has at least two predecessors)
     for (int u = tm.t; u < V; u += NT)
-        for (int e = rp[u]; e < rp[u + 1]; e++) atomicAdd(&ws.indeg[col[e]], 1);
+        for (int e = rp[u]; e < rp[u + 1]; e++) atomicAdd(&ws.cnt[col[e]], 1);
     const int W = (V + 63) >> 6;
     for (int i = tm.t; i < V * W; i += NT) ws.anc[i] = 0;
     if (lead) sc[0] = 0;
@@ -204,8 +580,10 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     // ---- Kahn levels, and the ancestor closure pushed along each level's out-edges:
     //      everything that reaches u, and u itself, reaches each successor of u
     for (int v = tm.t; v < V; v += NT) {
-        ws.cnt[v] = ws.indeg[v];
-        if (ws.indeg[v] == 0) {
+        const int dg = ws.cnt[v];
+        ws.indeg[v] = (uint16_t)dg;
+        ws.st[v] = dg >= 2 ? ST_JOIN : 0;
+        if (dg == 0) {
             const int p = atomicAdd((int *)&sc[0], 1);
             ws.topo[p] = (uint16_t)v;
             if (a.o.level) a.o.level[n0 + v] = 0;
@@ -237,7 +615,7 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         const int ne = sc[0];
         tm.sync();
         L++;
-        if (lead) ws.lvl_off[L] = le;
+        if (lead) ws.lvl_off[L] = (uint16_t)le;
         ls = le;
         le = ne;
     }
@@ -269,6 +647,7 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             acc += (uint64_t)c << b;
         }
         ws.wanc[v] = acc;
+        if (a.o.wanc) a.o.wanc[n0 + v] = (int64_t)acc;
     }
     tm.sync();
 
@@ -280,55 +659,48 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     tm.sync();
     team_bitonic_sort(tm, ws.skey, P);
     // per sorted position: join flag (-> Theta index), start and end of its W^anc run
-    int32_t *jcnt = ws.lst, *rs = ws.cnt, *re = ws.gstart;
     for (int i = tm.t; i < V; i += NT) {
         const int v = (int)(ws.skey[i] & 0xffff);
         const uint64_t wv = ws.skey[i] >> 16;
-        jcnt[i] = ws.indeg[v] >= 2 ? 1 : 0;
-        rs[i] = (i == 0 || (ws.skey[i - 1] >> 16) != wv) ? i : 0;
-        re[i] = (i == V - 1 || (ws.skey[i + 1] >> 16) != wv) ? i : 0x7fffffff;
+        ws.jcnt[i] = (ws.st[v] & ST_JOIN) ? 1 : 0;
+        ws.rs[i] = (i == 0 || (ws.skey[i - 1] >> 16) != wv) ? i : 0;
+        ws.re[i] = (i == V - 1 || (ws.skey[i + 1] >> 16) != wv) ? i : 0x7fffffff;
     }
     tm.sync();
-    team_scan_inplace(tm, jcnt, V, [](uint64_t x, uint64_t y) { return x + y; }, false);
-    team_scan_inplace(tm, rs, V, [](uint64_t x, uint64_t y) { return x > y ? x : y; }, false);
-    team_scan_inplace(tm, re, V, [](uint64_t x, uint64_t y) { return x < y ? x : y; }, true);
-    const int N = jcnt[V - 1];  // number of join nodes
-    uint16_t *jidx = ws.rnd;    // Theta index of each join node
+    team_scan_inplace(tm, ws.jcnt, V, [](uint64_t x, uint64_t y) { return x + y; }, false);
+    team_scan_inplace(tm, ws.rs, V, [](uint64_t x, uint64_t y) { return x > y ? x : y; }, false);
+    team_scan_inplace(tm, ws.re, V, [](uint64_t x, uint64_t y) { return x < y ? x : y; }, true);
+    const int N = ws.jcnt[V - 1];  // number of join nodes
     for (int i = tm.t; i < V; i += NT) {
         const int v = (int)(ws.skey[i] & 0xffff);
-        const int r = (V - 1 - re[i]) + (i - rs[i]);
+        const int r = (V - 1 - ws.re[i]) + (i - ws.rs[i]);
         ws.rank[v] = (uint16_t)r;
         ws.byrank[r] = (uint16_t)v;
-        if (ws.indeg[v] >= 2) jidx[v] = (uint16_t)(jcnt[i] - 1);
+        ws.pos[v] = (uint16_t)i;
+        ws.bk[v] = NONE16;
     }
     tm.sync();
 
     // ---- Eq.3 blocks: a node belongs to the first join (in Theta order) it is an ancestor
-    //      of, i.e. the smallest (W^anc, id) among the joins reachable from it; computed by
-    //      a min over successors in reverse level order. No reachable join: residual.
-    for (int v = tm.t; v < V; v += NT) ws.bk[v] = KEY_INF;
-    tm.sync();
+    //      of, i.e. the smallest sorted position among the joins reachable from it; computed
+    //      by a min over successors in reverse level order. No reachable join: residual.
     for (int l = nlev - 1; l >= 0; l--) {
         const int lb = ws.lvl_off[l], lend = (l + 1 < nlev) ? ws.lvl_off[l + 1] : V;
         for (int i = lb + tm.t; i < lend; i += NT) {
             const int v = ws.topo[i];
-            uint64_t b = KEY_INF;
+            int b = NONE16;
             for (int e = rp[v]; e < rp[v + 1]; e++) {
                 const int s = col[e];
-                if (ws.indeg[s] >= 2) {
-                    const uint64_t ks = (ws.wanc[s] << 16) | (uint64_t)s;
-                    b = ks < b ? ks : b;
-                }
-                const uint64_t bs = ws.bk[s];
-                b = bs < b ? bs : b;
+                if (ws.st[s] & ST_JOIN) b = min(b, (int)ws.pos[s]);
+                b = min(b, (int)ws.bk[s]);
             }
-            ws.bk[v] = b;
+            ws.bk[v] = (uint16_t)b;
         }
         tm.sync();
     }
     for (int v = tm.t; v < V; v += NT) {
-        const uint64_t b = ws.bk[v];
-        ws.blk[v] = b == KEY_INF ? N : (int)jidx[(int)(b & 0xffff)];
+        const int b = ws.bk[v];
+        ws.blk[v] = (uint16_t)(b == NONE16 ? N : ws.jcnt[b] - 1);
     }
     tm.sync();
 
@@ -351,7 +723,7 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     bad = false;
     for (int v = tm.t; v < V; v += NT) {
         if (ws.cnt[v] > 1) bad = true;
-        ws.st[v] = ws.cnt[v] == 0 ? ST_ACTIVE : 0;
+        ws.st[v] = (uint8_t)((ws.st[v] & ST_JOIN) | (ws.cnt[v] == 0 ? ST_ACTIVE : 0));
     }
     if (tm.any(bad)) {
         if (lead) write_failure(a, d, DAGRT_E_INTERNAL);
@@ -426,42 +798,47 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     const int G = ws.nround[N];
     for (int v = tm.t; v < V; v += NT) {
         const int b = ws.blk[v];
-        ws.group_of[v] = (b ? ws.nround[b - 1] : 0) + ws.rnd[v];
+        ws.group_of[v] = (uint16_t)((b ? ws.nround[b - 1] : 0) + ws.rnd[v]);
     }
     tm.sync();
 
     // ---- member lists of each group, ordered by id
-    for (int g = tm.t; g <= G; g += NT) {
-        ws.gfill[g] = 0;
-        ws.gstart[g + 1] = 0;
-    }
-    if (lead) ws.gstart[0] = 0;
+    for (int q = tm.t; q <= G; q += NT) ws.gfill[q] = 0;
     tm.sync();
-    for (int v = tm.t; v < V; v += NT) atomicAdd(&ws.gstart[ws.group_of[v] + 1], 1);
+    for (int v = tm.t; v < V; v += NT) atomicAdd(&ws.gfill[ws.group_of[v]], 1);
     tm.sync();
-    team_scan_inplace(tm, ws.gstart + 1, G, [](uint64_t x, uint64_t y) { return x + y; }, false);
+    team_scan_inplace(tm, ws.gfill, G, [](uint64_t x, uint64_t y) { return x + y; }, false);
+    for (int q = tm.t; q <= G; q += NT) ws.gstart[q] = (uint16_t)(q ? ws.gfill[q - 1] : 0);
+    tm.sync();
+    for (int q = tm.t; q <= G; q += NT) ws.gfill[q] = 0;
+    tm.sync();
     for (int v = tm.t; v < V; v += NT) {
-        const int g = ws.group_of[v];
-        const int p = atomicAdd(&ws.gfill[g], 1);
-        ws.gtmp[ws.gstart[g] + p] = (uint16_t)v;
+        const int q = ws.group_of[v];
+        const int p = atomicAdd(&ws.gfill[q], 1);
+        ws.gtmp[ws.gstart[q] + p] = (uint16_t)v;
     }
     tm.sync();
     for (int i = tm.t; i < V; i += NT) {
         const int v = ws.gtmp[i];
-        const int g = ws.group_of[v];
+        const int q = ws.group_of[v];
         int pos = 0;
-        for (int j = ws.gstart[g]; j < ws.gstart[g + 1]; j++) pos += ws.gtmp[j] < v;
-        ws.gmem[ws.gstart[g] + pos] = (uint16_t)v;
+        for (int x = ws.gstart[q]; x < ws.gstart[q + 1]; x++) pos += ws.gtmp[x] < v;
+        ws.gmem[ws.gstart[q] + pos] = (uint16_t)v;
     }
     tm.sync();
 
     // ---- Alg.2 over the groups in order, with Lemma 1 and Theorem 1
+    int nsrc = 0;
     for (int v = tm.t; v < V; v += NT) {
-        ws.rem[v] = ws.load[v];
+        const uint32_t x = ws.load[v];
+        ws.rem[v] = x;
+        ws.cfull[v] = (uint32_t)exec_time(x, ws.kk[v], x < M ? x : M, M);
         ws.cnt[v] = ws.indeg[v];  // predecessors not yet finished
         ws.st[v] = 0;
         ws.mm[v] = 0;
+        nsrc += ws.indeg[v] == 0;
     }
+    nsrc = (int)tm.sum(nsrc);
     for (int w = tm.t; w < W; w += NT) ws.relmask[w] = 0;
     tm.sync();
     // released set as a bit mask over ranks (W^anc descending), so the next parallel
@@ -471,252 +848,61 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             atomicOr((unsigned long long *)&ws.relmask[ws.rank[v] >> 6], 1ull << (ws.rank[v] & 63));
     tm.sync();
 
-    const int64_t rbase = 2 * n0;
-    const bool want_edges = a.o.extra_off != nullptr;
-    int64_t ecap = 0, ebase = 0;
-    if (want_edges) {
-        ebase = a.o.extra_off[d];
-        ecap = a.o.extra_off[d + 1] - ebase;
-    }
-    uint64_t bound = 0;
-    int64_t nextra = 0;
-    int nrows = 0, nseg = 0;
-    bool internal_err = false;
-
-    for (int j = 0; j < G; j++) {
-        const int gb = ws.gstart[j], ge = ws.gstart[j + 1];
-        uint32_t cm = 0;
-        uint64_t wl = 0;
-        for (int i = gb + tm.t; i < ge; i += NT) {
-            const int v = ws.gmem[i];
-            if (!(ws.st[v] & ST_DONE)) {
-                cm++;
-                wl += ws.rem[v];
-            }
-        }
-        const uint32_t np = (uint32_t)tm.sum(cm);
-        if (np == 0) {  // every member already ran as a parallel node: the group is dropped
-            if (lead && a.o.group_R) a.o.group_R[n0 + j] = 0;
-            continue;
-        }
-        const uint64_t Wg = tm.sum(wl);
-        // Eq.5: m_i = min(m_i^max, round(C^_i M / W(pi_j))), half up, >= 1
-        uint64_t sml = 0;
-        for (int i = gb + tm.t; i < ge; i += NT) {
-            const int v = ws.gmem[i];
-            if (ws.st[v] & ST_DONE) continue;
-            uint64_t r = (2ull * ws.rem[v] * M + Wg) / (2ull * Wg);
-            if (r < 1) r = 1;
-            const uint32_t m = (uint32_t)(r < ws.rem[v] ? r : ws.rem[v]);
-            ws.mm[v] = (uint16_t)m;
-            sml += m;
-        }
-        uint64_t sum_m = tm.sum(sml);
-        tm.sync();
-        while (sum_m > M) {  // keep sum m_i <= M: trim the largest m (ties: higher id)
-            uint64_t key = 0;
-            for (int i = gb + tm.t; i < ge; i += NT) {
-                const int v = ws.gmem[i];
-                if (ws.st[v] & ST_DONE) continue;
-                const uint64_t kv = ((uint64_t)ws.mm[v] << 16) | (uint64_t)v;
-                key = kv > key ? kv : key;
-            }
-            key = tm.maxu(key);
-            if (lead) ws.mm[key & 0xffff]--;
-            sum_m--;
+    Dag g;
+    g.n0 = n0;
+    g.rbase = 2 * n0;
+    g.V = V;
+    g.W = W;
+    g.M = M;
+    g.variant = a.variant;
+    g.rp = rp;
+    g.col = col;
+    g.want_edges = a.o.extra_off != nullptr;
+    g.ebase = g.want_edges ? a.o.extra_off[d] : 0;
+    g.ecap = g.want_edges ? a.o.extra_off[d + 1] - g.ebase : 0;
+    Acc acc;
+    acc.bound = 0;
+    acc.nextra = 0;
+    acc.nrows = 0;
+    acc.nseg = 0;
+    acc.nrel = nsrc;
+    acc.err = false;
+    constexpr int kSerialMax = NT == 32 ? 8 : 32;  // larger groups use the whole team
+    for (int j = 0; j < G;) {
+        int j1 = j;
+        while (j1 < G && ws.gstart[j1 + 1] - ws.gstart[j1] <= kSerialMax) j1++;
+        if (lead)
+            for (int q = j; q < j1; q++) group_serial(ws, a, g, q, acc);
+        if (j1 < G) {
+            if (lead) sc[8] = acc.nrows;
             tm.sync();
-        }
-        // Eq.1 per member; Lemma 1: R(pi_j) = max C_i; v_R = lowest id with C_i = R
-        uint64_t cmax = 0;
-        for (int i = gb + tm.t; i < ge; i += NT) {
-            const int v = ws.gmem[i];
-            if (ws.st[v] & ST_DONE) continue;
-            const uint64_t c = exec_time(ws.rem[v], ws.kk[v], ws.mm[v], M);
-            cmax = c > cmax ? c : cmax;
-        }
-        const uint64_t R = tm.maxu(cmax);
-        uint64_t vr = KEY_INF;
-        for (int i = gb + tm.t; i < ge; i += NT) {
-            const int v = ws.gmem[i];
-            if (ws.st[v] & ST_DONE) continue;
-            if (exec_time(ws.rem[v], ws.kk[v], ws.mm[v], M) == R) vr = (uint64_t)v < vr ? (uint64_t)v : vr;
-        }
-        const int vR = (int)tm.minu(vr);
-        const uint32_t S0 = M - (uint32_t)sum_m;  // Eq.6: remaining SMs
-        // plan rows of the members, by id
-        for (int base = gb; base < ge; base += NT) {
-            const int i = base + tm.t;
-            const bool mem = i < ge && !(ws.st[ws.gmem[i]] & ST_DONE);
-            uint32_t tot;
-            const uint32_t off = tm.excl_sum(mem ? 1u : 0u, &tot);
-            if (mem) {
-                const int v = ws.gmem[i];
-                const int r = nrows + (int)off;
-                if (r < 2 * V)
-                    write_row(a, rbase, r, v, j, ws.rem[v], ws.kk[v], ws.mm[v],
-                              exec_time(ws.rem[v], ws.kk[v], ws.mm[v], M), false);
-            }
-            nrows += (int)tot;
+            group_team(tm, ws, a, g, j1, acc);
         }
         tm.sync();
-
-        // Alg.2 lines 7-17: parallel nodes by descending W^anc (lowest rank first)
-        if (lead) {
-            int nl = 0, nwhole = 0, nr = nrows, ns = nseg;
-            if (variant != DAGRT_VAR_NOPARA) {
-                uint32_t S = S0;
-                uint64_t WS = R * (uint64_t)S0;  // Eq.6
-                bool stop = false;
-                for (int w = 0; w < W && !stop; w++) {
-                    uint64_t bits = ws.relmask[w];
-                    while (bits) {
-                        const int b = __ffsll((long long)bits) - 1;
-                        bits &= bits - 1;
-                        const int u = ws.byrank[w * 64 + b];
-                        if (ws.group_of[u] == j) continue;  // a member of pi_j
-                        const uint32_t load = ws.rem[u], k = ws.kk[u];
-                        bool split = false;
-                        uint32_t mu = 0;
-                        uint64_t p = 0;
-                        if (variant == DAGRT_VAR_LITERAL) {
-                            if (WS == 0) { stop = true; break; }
-                            if (load > WS) {
-                                split = true;
-                                p = WS;
-                                mu = (uint32_t)(p < S ? p : S);
-                            } else {
-                                mu = load < S ? load : S;
-                                WS -= load;
-                            }
-                        } else {
-                            if (S == 0) { stop = true; break; }
-                            mu = load < S ? load : S;
-                            if (exec_time(load, k, mu, M) > R) {
-                                if (variant == DAGRT_VAR_NOSEG) continue;
-                                split = true;
-                                p = split_size(load, k, S, R);
-                                mu = (uint32_t)(p < S ? p : S);
-                            } else {
-                                S -= mu;
-                            }
-                        }
-                        if (split) {  // node segmentation: the parallel part runs now
-                            const int s = ns++;
-                            if (a.o.seg_parent) {
-                                a.o.seg_parent[n0 + s] = u;
-                                a.o.seg_load[n0 + s] = (int64_t)p;
-                                a.o.seg_m[n0 + s] = (int32_t)mu;
-                                a.o.seg_group[n0 + s] = j;
-                            }
-                            if (nr < 2 * V)
-                                write_row(a, rbase, nr, V + s, j, (uint32_t)p, k, mu,
-                                          exec_time(p, k, mu, M), false);
-                            nr++;
-                            ws.rem[u] = load - (uint32_t)p;
-                            ws.lst[nl++] = V + s;
-                            stop = true;
-                            break;
-                        }
-                        ws.st[u] |= ST_LAUNCH;
-                        ws.mm[u] = (uint16_t)mu;
-                        if (nr < 2 * V)
-                            write_row(a, rbase, nr, u, j, load, k, mu, exec_time(load, k, mu, M), false);
-                        nr++;
-                        ws.lst[nl++] = u;
-                        nwhole++;
-                    }
-                }
-            }
-            if (nr - 1 < 2 * V) a.plan_mkf[rbase + nr - 1] |= 1u << 24;  // last row of pi_j
-            if (nr > 2 * V || ns > V) internal_err = true;
-            sc[1] = nl;
-            sc[2] = nwhole;
-            sc[3] = nr;
-            sc[4] = ns;
-            sc[5] = internal_err;
-        }
-        tm.sync();
-        const int nl = sc[1], nwhole = sc[2];
-        nrows = sc[3];
-        nseg = sc[4];
-
-        // extra dependencies: (v_n, succ(v_R)) for launched parts, (v_R, v_n) for the
-        // unlaunched parallel nodes (the split node's residual included)
-        const int outdeg = rp[vR + 1] - rp[vR];
-        uint32_t qp = 0;
-        for (int w = tm.t; w < W; w += NT) qp += __popcll(ws.relmask[w]);
-        const int64_t nq = (int64_t)tm.sum(qp) - np;  // |para(pi_j)|
-        if (variant != DAGRT_VAR_NOPARA) {
-            if (want_edges && lead) {
-                int64_t idx = nextra;
-                for (int i = 0; i < nl; i++)
-                    for (int e = rp[vR]; e < rp[vR + 1]; e++, idx++)
-                        if (idx < ecap) {
-                            a.o.extra_src[ebase + idx] = ws.lst[i];
-                            a.o.extra_dst[ebase + idx] = col[e];
-                        }
-                for (int w = 0; w < W; w++) {
-                    uint64_t bits = ws.relmask[w];
-                    while (bits) {
-                        const int b = __ffsll((long long)bits) - 1;
-                        bits &= bits - 1;
-                        const int u = ws.byrank[w * 64 + b];
-                        if (ws.group_of[u] == j || (ws.st[u] & ST_LAUNCH)) continue;
-                        if (idx < ecap) {
-                            a.o.extra_src[ebase + idx] = vR;
-                            a.o.extra_dst[ebase + idx] = u;
-                        }
-                        idx++;
-                    }
-                }
-            }
-            nextra += (int64_t)nl * outdeg + (nq - nwhole);
-        }
-        tm.sync();
-
-        // members and whole launches finish with pi_j: release their successors
-        for (int i = gb + tm.t; i < ge + nl; i += NT) {
-            int v;
-            if (i < ge) {
-                v = ws.gmem[i];
-                if (ws.st[v] & ST_DONE) continue;
-            } else {
-                v = ws.lst[i - ge];
-                if (v >= V) continue;  // a segment: its node is not finished
-            }
-            ws.st[v] = ST_DONE;
-            ws.rem[v] = 0;
-            if (a.o.exec_group) a.o.exec_group[n0 + v] = j;
-            atomicAnd((unsigned long long *)&ws.relmask[ws.rank[v] >> 6], ~(1ull << (ws.rank[v] & 63)));
-            for (int e = rp[v]; e < rp[v + 1]; e++) {
-                const int s = col[e];
-                if (atomicSub(&ws.cnt[s], 1) == 1)
-                    atomicOr((unsigned long long *)&ws.relmask[ws.rank[s] >> 6], 1ull << (ws.rank[s] & 63));
-            }
-        }
-        if (lead && a.o.group_R) a.o.group_R[n0 + j] = (int64_t)R;
-        bound += R;
-        tm.sync();
+        j = j1 + 1;
     }
-    internal_err = sc[5] != 0 && G > 0;
 
     // ---- per-DAG and per-node outputs
-    int code = DAGRT_OK;
-    if (internal_err) code = DAGRT_E_INTERNAL;
-    else if (want_edges && nextra > ecap) code = DAGRT_E_CAP;
     if (lead) {
+        // candidate bounds fit 32-bit arithmetic: loads < 2^17 and every group sum of
+        // C <= ceil(255/M) * max C^ over at most 2V rows below 2^31
+        const uint64_t waves = (255 + M - 1) / M;
+        a.pflag[d] = (mx < (1ull << 17) && mx * waves * 2ull * (uint64_t)V < (1ull << 31)) ? 1 : 0;
+        int code = DAGRT_OK;
+        if (acc.err) code = DAGRT_E_INTERNAL;
+        else if (g.want_edges && acc.nextra > g.ecap) code = DAGRT_E_CAP;
+        const int64_t bnd = code == DAGRT_E_INTERNAL ? -1 : (int64_t)acc.bound;
         a.status[d] = code;
-        a.bound[d] = code == DAGRT_E_INTERNAL ? -1 : (int64_t)bound;
-        a.nrows[d] = nrows;
+        a.bound[d] = bnd;
+        a.nrows[d] = acc.nrows;
         if (a.o.status) a.o.status[d] = code;
-        if (a.o.bound) a.o.bound[d] = code == DAGRT_E_INTERNAL ? -1 : (int64_t)bound;
+        if (a.o.bound) a.o.bound[d] = bnd;
         if (a.o.n_groups) a.o.n_groups[d] = G;
-        if (a.o.n_seg) a.o.n_seg[d] = nseg;
-        if (a.o.n_rows) a.o.n_rows[d] = nrows;
-        if (a.o.n_extra) a.o.n_extra[d] = nextra;
+        if (a.o.n_seg) a.o.n_seg[d] = acc.nseg;
+        if (a.o.n_rows) a.o.n_rows[d] = acc.nrows;
+        if (a.o.n_extra) a.o.n_extra[d] = acc.nextra;
     }
     for (int v = tm.t; v < V; v += NT) {
-        if (a.o.wanc) a.o.wanc[n0 + v] = (int64_t)ws.wanc[v];
         if (a.o.block_of) a.o.block_of[n0 + v] = ws.blk[v];
         if (a.o.group_of) a.o.group_of[n0 + v] = ws.group_of[v];
         if (a.o.m) a.o.m[n0 + v] = ws.mm[v];
@@ -730,15 +916,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_sched_warp(SchedArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     Ws ws;
-    const int64_t bytes = ws_carve(nullptr, VC, nullptr);
-    ws_carve(smem + warp * bytes, VC, &ws);
+    const int64_t bytes = ws_carve(nullptr, VC, kEdgesPerNode * VC, nullptr);
+    ws_carve(smem + warp * bytes, VC, kEdgesPerNode * VC, &ws);
     Team<32> tm{(int)(threadIdx.x & 31), nullptr};
     for (;;) {
         int idx = 0;
         if (tm.t == 0) idx = atomicAdd(a.counter, 1);
         idx = __shfl_sync(FULL, idx, 0);
         if (idx >= a.n_list) break;
-        schedule_one<32>(tm, ws, a, a.list[idx], VC);
+        schedule_one<32>(tm, ws, a, a.list[idx], VC, kEdgesPerNode * VC);
         __syncwarp();
     }
 }
@@ -748,7 +934,7 @@ __global__ void __launch_bounds__(NT) k_sched_cta(SchedArgs a) {
     __shared__ uint64_t red[NT / 32];
     __shared__ int idx_s;
     Ws ws;
-    ws_carve(a.gws + (int64_t)blockIdx.x * a.gws_stride, a.vcap, &ws);
+    ws_carve(a.gws + (int64_t)blockIdx.x * a.gws_stride, a.vcap, a.ecap, &ws);
     Team<NT> tm{(int)threadIdx.x, red};
     for (;;) {
         if (threadIdx.x == 0) idx_s = atomicAdd(a.counter, 1);
@@ -756,7 +942,7 @@ __global__ void __launch_bounds__(NT) k_sched_cta(SchedArgs a) {
         const int idx = idx_s;
         __syncthreads();
         if (idx >= a.n_list) break;
-        schedule_one<NT>(tm, ws, a, a.list[idx], a.vcap);
+        schedule_one<NT>(tm, ws, a, a.list[idx], a.vcap, a.ecap);
         __syncthreads();
     }
 }
@@ -764,7 +950,7 @@ __global__ void __launch_bounds__(NT) k_sched_cta(SchedArgs a) {
 // ------------------------------------------------------------------ launchers
 template <int VC>
 static cudaError_t launch_warp(const SchedArgs &a, int n_sm, cudaStream_t st) {
-    const int64_t bytes = ws_carve(nullptr, VC, nullptr) * kWarpsPerCta;
+    const int64_t bytes = ws_carve(nullptr, VC, kEdgesPerNode * VC, nullptr) * kWarpsPerCta;
     cudaError_t e = cudaFuncSetAttribute(k_sched_warp<VC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e != cudaSuccess) return e;
@@ -784,6 +970,7 @@ cudaError_t sched_launch_warp(int vc, const SchedArgs &a, int n_sm, cudaStream_t
     switch (vc) {
         case 64: return launch_warp<64>(a, n_sm, st);
         case 128: return launch_warp<128>(a, n_sm, st);
+        case 192: return launch_warp<192>(a, n_sm, st);
         case 256: return launch_warp<256>(a, n_sm, st);
         default: return cudaErrorInvalidValue;
     }

@@ -4,12 +4,13 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/dagrt.h"
+#include "dagrt.h"
 
 namespace dagrt {
 
-constexpr int kWarpsPerCta = 4;    // independent warp teams per CTA (small DAGs)
+constexpr int kWarpsPerCta = 2;    // independent warp teams per CTA (small DAGs)
 constexpr int kCtaThreads = 256;   // threads of a CTA team (large DAGs)
+constexpr int kEdgesPerNode = 12;  // edge capacity of a warp-team workspace, per node
 
 // Arguments of one scheduling launch. Every pointer is a device pointer.
 struct SchedArgs {
@@ -29,17 +30,17 @@ struct SchedArgs {
     int32_t *status;
     int64_t *bound;
     int32_t *nrows;
-    uint2 *plan_lc;      // {load, scheduled C}
-    uint32_t *plan_mkf;  // m | k << 16 | last-row-of-group << 24
+    int32_t *pflag;      // per DAG: bit 0 = candidate bounds of this DAG fit 32-bit sums
+    uint4 *plan;         // rows {load, scheduled C, m | k << 16 | last-row-of-group << 24, 0}
     // optional caller outputs (device pointers, NULL = skip)
     dagrt_schedule_out o;
     // global workspace of the CTA-team kernel
     unsigned char *gws;
     int64_t gws_stride;
-    int32_t vcap;
+    int32_t vcap, ecap;
 };
 
-int64_t sched_ws_bytes(int vc);
+int64_t sched_ws_bytes(int vc, int ec);
 cudaError_t sched_launch_warp(int vc, const SchedArgs &a, int n_sm, cudaStream_t st);
 int sched_cta_grid(int n_sm);
 cudaError_t sched_launch_cta(const SchedArgs &a, int grid, cudaStream_t st);
