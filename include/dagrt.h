@@ -182,6 +182,33 @@ int dagrt_bound(dagrt_batch *batch, int32_t n_variants, const int32_t *variant_i
                 int32_t n_alloc, const uint8_t *m_alloc, int64_t cand_stride,
                 int64_t *out_bound, int64_t *best_bound, int32_t *best_cand, uint32_t flags);
 
+/* Scheduler entry point for callers that cannot allocate device memory at run time:
+ * real-time executives that reserve every buffer before their task set starts (an
+ * allocation may block for an unbounded time), work recorded into CUDA graphs or run under
+ * a memory budget owned by someone else, and plug-ins whose host framework forbids
+ * cudaMalloc. The paper has no counterpart; it is an operational variant of
+ * dagrt_load_csr + dagrt_schedule(variant) that keeps only each DAG's bound and status.
+ *
+ * It allocates nothing: the scheduler's scratch (the per-team workspaces of the large-DAG
+ * kernel and its work counter) lives in one fixed 4 MiB __device__ array inside the
+ * library, which every GPU that loads the library holds until the process exits. All
+ * array arguments are device pointers with dagrt_load_csr's layout; bound[n_dags] and
+ * status[n_dags] receive dagrt_schedule's values. DAGs of more than 512 nodes or 8192 edges
+ * (or with negative node/edge counts) are rejected with status DAGRT_E_INVAL and bound -1.
+ * The call only enqueues work on `cuda_stream` (a cudaStream_t, NULL = legacy default);
+ * results are valid once the caller synchronises that stream.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before capturing any stream into a graph. Every call shares the
+ * array and resets its counter, so calls whose kernels overlap on the GPU (two streams,
+ * two host threads) race and give wrong results: order them.
+ * Returns DAGRT_OK, DAGRT_E_INVAL (NULL pointer, n_dags < 0, M or variant out of range) or
+ * DAGRT_E_DEVICE (a CUDA call failed). */
+int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_t *edge_off,
+                           const int32_t *row_ptr, const int32_t *col, const int64_t *wcet,
+                           const uint8_t *k64, int32_t M, int32_t variant, int64_t *bound,
+                           int32_t *status, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -446,6 +446,7 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
     a.variant = variant;
     a.status = p.status;
     a.bound = p.bound;
+    a.oversize_status = DAGRT_E_INTERNAL;  // the size classes guarantee every DAG fits
     a.nrows = p.nrows;
     a.pflag = p.pflag;
     a.plan = p.rows;

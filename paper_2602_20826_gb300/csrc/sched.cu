@@ -146,7 +146,7 @@ struct Acc {
 __device__ inline void write_failure(const SchedArgs &a, int d, int code) {
     a.status[d] = code;
     a.bound[d] = -1;
-    a.nrows[d] = 0;
+    if (a.nrows) a.nrows[d] = 0;
     if (a.o.status) a.o.status[d] = code;
     if (a.o.bound) a.o.bound[d] = -1;
     if (a.o.n_groups) a.o.n_groups[d] = 0;
@@ -159,7 +159,7 @@ __device__ inline void write_row(const SchedArgs &a, const Dag &g, int r, int id
                                  uint32_t k, uint32_t m, uint64_t c) {
     if (r >= 2 * g.V) return;
     const int64_t i = g.rbase + r;
-    a.plan[i] = make_uint4(load, (uint32_t)c, m | (k << 16), 0u);
+    if (a.plan) a.plan[i] = make_uint4(load, (uint32_t)c, m | (k << 16), 0u);
     if (a.o.row_id) a.o.row_id[i] = id;
     if (a.o.row_group) a.o.row_group[i] = group;
     if (a.o.row_m0) a.o.row_m0[i] = (int32_t)m;
@@ -237,7 +237,7 @@ __device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, 
             }
         }
     }
-    if (acc.nrows - 1 < 2 * g.V) a.plan[g.rbase + acc.nrows - 1].z |= 1u << 24;  // last row of pi_j
+    if (a.plan && acc.nrows - 1 < 2 * g.V) a.plan[g.rbase + acc.nrows - 1].z |= 1u << 24;  // last row of pi_j
     if (acc.nrows > 2 * g.V || acc.nseg > g.V) acc.err = true;
     *nl_out = nl;
     *nwhole_out = nwhole;
@@ -500,8 +500,8 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     volatile int32_t *sc = ws.sc;
     const bool lead = tm.t == 0;
 
-    if (V > vc || E > ec) {  // routed to the wrong size class: never expected
-        if (lead) write_failure(a, d, DAGRT_E_INTERNAL);
+    if (V < 0 || E < 0 || V > vc || E > ec) {  // does not fit this workspace
+        if (lead) write_failure(a, d, a.oversize_status);
         return;
     }
 
@@ -557,7 +557,7 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         if (lead) {
             a.status[d] = DAGRT_OK;
             a.bound[d] = 0;
-            a.nrows[d] = 0;
+            if (a.nrows) a.nrows[d] = 0;
             if (a.o.status) a.o.status[d] = DAGRT_OK;
             if (a.o.bound) a.o.bound[d] = 0;
             if (a.o.n_groups) a.o.n_groups[d] = 0;
@@ -887,14 +887,14 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         // candidate bounds fit 32-bit arithmetic: loads < 2^17 and every group sum of
         // C <= ceil(255/M) * max C^ over at most 2V rows below 2^31
         const uint64_t waves = (255 + M - 1) / M;
-        a.pflag[d] = (mx < (1ull << 17) && mx * waves * 2ull * (uint64_t)V < (1ull << 31)) ? 1 : 0;
+        if (a.pflag) a.pflag[d] = (mx < (1ull << 17) && mx * waves * 2ull * (uint64_t)V < (1ull << 31)) ? 1 : 0;
         int code = DAGRT_OK;
         if (acc.err) code = DAGRT_E_INTERNAL;
         else if (g.want_edges && acc.nextra > g.ecap) code = DAGRT_E_CAP;
         const int64_t bnd = code == DAGRT_E_INTERNAL ? -1 : (int64_t)acc.bound;
         a.status[d] = code;
         a.bound[d] = bnd;
-        a.nrows[d] = acc.nrows;
+        if (a.nrows) a.nrows[d] = acc.nrows;
         if (a.o.status) a.o.status[d] = code;
         if (a.o.bound) a.o.bound[d] = bnd;
         if (a.o.n_groups) a.o.n_groups[d] = G;
@@ -942,7 +942,7 @@ __global__ void __launch_bounds__(NT) k_sched_cta(SchedArgs a) {
         const int idx = idx_s;
         __syncthreads();
         if (idx >= a.n_list) break;
-        schedule_one<NT>(tm, ws, a, a.list[idx], a.vcap, a.ecap);
+        schedule_one<NT>(tm, ws, a, a.list ? a.list[idx] : idx, a.vcap, a.ecap);
         __syncthreads();
     }
 }

@@ -22,13 +22,17 @@ struct SchedArgs {
     const uint8_t *k64;
     int32_t M;
     int32_t variant;
-    // DAGs of this size class and the work-stealing counter over them
+    // DAGs of this size class (NULL: DAGs 0 .. n_list-1 in order) and the work-stealing
+    // counter over them
     const int32_t *list;
     int32_t n_list;
     int32_t *counter;
-    // always written: per-DAG status, bound, plan row count; plan rows at 2*node_off[d]
+    // always written: per-DAG status and bound
     int32_t *status;
     int64_t *bound;
+    // status of a DAG larger than the workspace (or with negative offsets)
+    int32_t oversize_status;
+    // plan of the schedule (NULL: not kept): row count, flags, rows at 2*node_off[d]
     int32_t *nrows;
     int32_t *pflag;      // per DAG: bit 0 = candidate bounds of this DAG fit 32-bit sums
     uint4 *plan;         // rows {load, scheduled C, m | k << 16 | last-row-of-group << 24, 0}

@@ -59,6 +59,8 @@ dagrt_batch_total_nodes = _sig("dagrt_batch_total_nodes", C.c_int64, [_vp])
 dagrt_schedule = _sig("dagrt_schedule", C.c_int, [_vp, C.c_int32, C.POINTER(dagrt_schedule_out), C.c_uint32])
 dagrt_bound = _sig("dagrt_bound", C.c_int,
                    [_vp, C.c_int32, C.POINTER(C.c_int32), C.c_int32, _vp, C.c_int64, _vp, _vp, _vp, C.c_uint32])
+dagrt_schedule_noalloc = _sig("dagrt_schedule_noalloc", C.c_int,
+                              [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp])
 
 
 class DagrtError(RuntimeError):
@@ -227,3 +229,13 @@ class LoadedBatch:
         self.ctx.check(rc)
         return (ob[:self.n_dags * n_cand].reshape(self.n_dags, n_cand) if want_all else None,
                 bb[:self.n_dags], bc[:self.n_dags])
+
+
+def schedule_noalloc(dev: dict, M: int, variant: int, bound, status, stream=None) -> int:
+    """dagrt_schedule_noalloc on a batch held in torch CUDA tensors (keys as for
+    Context.load); bound and status are torch CUDA tensors of n_dags entries. Enqueues
+    only; returns the C status code."""
+    n = int(dev["node_off"].shape[0]) - 1
+    return int(dagrt_schedule_noalloc(n, _ptr(dev["node_off"]), _ptr(dev["edge_off"]), _ptr(dev["row_ptr"]),
+                                      _ptr(dev["col"]), _ptr(dev["wcet"]), _ptr(dev["k64"]), int(M),
+                                      int(variant), _ptr(bound), _ptr(status), stream))
