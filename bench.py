@@ -21,6 +21,8 @@ from __future__ import annotations
 import argparse
 import json
 import os
+
+import numpy as np
 import subprocess
 import sys
 import tempfile
@@ -42,6 +44,8 @@ def _args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="dagrt", choices=["dagrt", "reference"])
+    p.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3-bound"],
+                   help="cfg2: the headline step; cfg3-bound: candidate bounds of config 3")
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="bounded CPU work of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -98,6 +102,70 @@ def _peaks():
         return float(pk["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def traffic(kernel: str, source: str):
+    """DRAM bytes per launch from the committed ncu capture, or None when the kernel's
+    source changed since the capture (profiles/traffic.json records its sha256)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, "paper_2602_20826_gb300", "csrc", source), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        return rec["bytes_per_launch"] if rec["source_sha256"] == sha else None
+    except Exception:
+        return None
+
+
+def run_cfg3_bound(args):
+    """Candidate bounds of config 3: 1,000 DAGs x (4 variants x 64 allocations from
+    {1,...,32}, allocation 0 = the schedule's own), materialised in HBM, argmin per DAG."""
+    import torch
+    from paper_2602_20826_gb300 import workloads as wl
+    from paper_2602_20826_gb300.dagrt import Context
+    torch.cuda.set_device(0)
+    b = wl.config(3)
+    stream = torch.cuda.current_stream()
+    ctx = Context(0, stream.cuda_stream)
+    lb = ctx.load(b)
+    for v in range(4):
+        lb.schedule(v, fields=("status",))
+    alloc, stride = wl.candidate_allocations(b, 4, 64, [1, 2, 4, 8, 16, 32], seed=wl.BASE_SEED + 13)
+    da = torch.from_numpy(alloc).cuda()
+    nd, nc = b.n_dags, 256
+    ob = torch.zeros(nd * nc, dtype=torch.int64, device="cuda")
+    bb = torch.zeros(nd, dtype=torch.int64, device="cuda")
+    bc = torch.zeros(nd, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        lb.bound([0, 1, 2, 3], 64, da, stride, ob, bb, bc)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        lb.bound([0, 1, 2, 3], 64, da, stride, ob, bb, bc)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(c) for a, c in evs) / 1e3 / args.steps
+    # rows read per DAG: the largest plan over the four variants
+    peak, kind = _peaks()
+    rmax = np.zeros(nd, np.int64)
+    for v in range(4):
+        rmax = np.maximum(rmax, lb.schedule(v, fields=("n_rows",))["n_rows"])
+    alg = int(rmax.sum()) * stride + 4 * 16 * int(rmax.sum()) + nd * nc * 8 + nd * 12
+    line = {"metric": "exact candidate-bound evals/s", "value": nd * nc / t, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "config 3: 1,000 ER DAGs 50-500 nodes p=0.05, M=148, 4 variants x 64 "
+                                   "allocations from {1..32} materialised in HBM, argmin per DAG",
+                       "l2": "flushed between steps (256 MB write)"},
+            "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / t / 1e9 / peak, "traffic": traffic("k_bound_tma", "bound.cu"),
+                         "kernel": "k_bound_tma", "alg_bytes_per_launch": alg,
+                         "peak_source": f"{kind} hbm_gbs"}}
+    print(json.dumps(line), flush=True)
 
 
 def cpu_baseline(batch, seconds: float, gpu_bounds=None):
@@ -163,6 +231,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "cfg3-bound":
+        import numpy as np  # noqa: F401
+        run_cfg3_bound(args)
         return
     if args.warmup < 3:
         args.warmup = 3
@@ -283,7 +355,7 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic("k_sched_warp", "sched.cu"),
                      "kernel": "k_sched_warp (all size classes of one dagrt_schedule call)",
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "alg_bytes_per_launch": alg_bytes, "kernel_ms": 1e3 * t_kern / args.steps},

@@ -182,6 +182,30 @@ int dagrt_bound(dagrt_batch *batch, int32_t n_variants, const int32_t *variant_i
                 int32_t n_alloc, const uint8_t *m_alloc, int64_t cand_stride,
                 int64_t *out_bound, int64_t *best_bound, int32_t *best_cand, uint32_t flags);
 
+/* Schedule search over generated candidate allocations (the problem formulation of Sec.
+ * 2.2: choose m_i and the DAG structure to minimise the bound). Candidate c =
+ * v * n_alloc + a of DAG d runs on the plan of structure variant variant_ids[v] (each must
+ * have been scheduled on the batch); allocation a = 0 keeps the schedule's own m, and for
+ * a > 0 plan row r gets levels[i] with i drawn by a counter-based generator: x = seed +
+ * (d << 40 | c << 20 | r), z = SplitMix64(x) (Steele, Lea and Flood, OOPSLA 2014),
+ * i = ((z >> 32) * n_levels) >> 32. Every candidate's bound is exact (as dagrt_bound).
+ * Limits: n_variants * n_alloc <= 2^20, n_levels in [1, 16], levels in [1, 255]. */
+typedef struct {
+    int32_t n_variants;
+    const int32_t *variant_ids;  /* host array */
+    int32_t n_alloc;
+    int32_t n_levels;
+    const uint8_t *levels;       /* host array */
+    uint64_t seed;
+} dagrt_search_cfg;
+
+/* out_bound [n_dags * n_cand] (may be NULL); best_bound, best_cand [n_dags] as in
+ * dagrt_bound (may be NULL); best_m [2*total_nodes] (may be NULL) receives the winning
+ * allocation in rows [2*node_off[d], 2*node_off[d] + n_rows) of the winning variant's plan
+ * (0 = keep the scheduled m). flags: DAGRT_PTR_DEVICE if the outputs are device pointers. */
+int dagrt_search(dagrt_batch *batch, const dagrt_search_cfg *cfg, int64_t *out_bound,
+                 int64_t *best_bound, int32_t *best_cand, uint8_t *best_m, uint32_t flags);
+
 /* Scheduler entry point for callers that cannot allocate device memory at run time:
  * real-time executives that reserve every buffer before their task set starts (an
  * allocation may block for an unbounded time), work recorded into CUDA graphs or run under

@@ -62,6 +62,10 @@ def lib():
                                          C.POINTER(_Out)]
         _lib.or_bound_plan.restype = C.c_int64
         _lib.or_bound_plan.argtypes = [C.c_int32, _P64, _P32, _P32, _P32, C.c_int32, _PU8, C.c_int64]
+        _lib.or_splitmix64.restype = C.c_uint64
+        _lib.or_splitmix64.argtypes = [C.c_uint64]
+        _lib.or_gen_level.restype = C.c_int32
+        _lib.or_gen_level.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, C.c_int32]
         _lib.or_schedule_batch.restype = C.c_int64
         _lib.or_schedule_batch.argtypes = [C.c_int32, _P64, _P64, _P32, _P32, _P64, _PU8, C.c_int32,
                                            C.c_int32, _P64, _P32]
@@ -193,3 +197,38 @@ def search_dag(batch, d: int, alloc, cand_stride: int, n_variants: int, n_alloc:
             out[c] = bound_plan(plan, batch.M, np.ascontiguousarray(col), 1)
     best = int(np.argmin(out)) if len(out) else -1
     return out, (int(out[best]) if best >= 0 else 0), best
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().or_splitmix64(C.c_uint64(x & (2**64 - 1))))
+
+
+def generated_allocation(seed: int, d: int, c: int, n_rows: int, levels, n_alloc: int):
+    """Allocation of generated candidate c of DAG d over n_rows plan rows (uint8 array):
+    zeros (keep the schedule) when c is the first allocation of its variant."""
+    out = np.zeros(max(n_rows, 1), np.uint8)[:n_rows]
+    if c % n_alloc == 0:
+        return out
+    L = lib()
+    for r in range(n_rows):
+        out[r] = levels[L.or_gen_level(C.c_uint64(seed), d, c, r, len(levels))]
+    return out
+
+
+def search_dag_generated(batch, d: int, variant_ids, n_alloc: int, levels, seed: int):
+    """Bounds of every generated candidate of DAG d and the argmin (min bound, lowest id)."""
+    plans = {}
+    nv = len(variant_ids)
+    out = np.zeros(nv * n_alloc, np.int64)
+    for vi, var in enumerate(variant_ids):
+        if var not in plans:
+            rc, plans[var] = schedule_dag_of(batch, d, int(var))
+            if rc != OK:
+                raise RuntimeError(f"oracle schedule failed: {rc}")
+        plan = plans[var]
+        for a in range(n_alloc):
+            c = vi * n_alloc + a
+            alloc = generated_allocation(seed, d, c, plan["n_rows"], levels, n_alloc)
+            out[c] = bound_plan(plan, batch.M, alloc if len(alloc) else None, 1)
+    best = int(np.argmin(out))
+    return out, int(out[best]), best

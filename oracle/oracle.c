@@ -574,3 +574,26 @@ int64_t or_schedule_batch(int32_t n_dags, const int64_t *node_off, const int64_t
     }
     return fails;
 }
+
+/* ------------------------------------------------- generated candidate search */
+
+/* SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+ * OOPSLA 2014): the output function applied to the counter x. */
+uint64_t or_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Level index of plan row r of candidate c of DAG d (candidates with allocation index 0
+ * keep the schedule: the caller handles them). The counter packs (d, c, r) as
+ * d << 40 | c << 20 | r added to the seed; the high 32 bits of the mixed value pick one of
+ * n_levels levels by multiply-shift. */
+int32_t or_gen_level(uint64_t seed, int64_t d, int64_t c, int64_t r, int32_t n_levels)
+{
+    uint64_t x = seed + (((uint64_t)d << 40) | ((uint64_t)c << 20) | (uint64_t)r);
+    uint64_t hi = or_splitmix64(x) >> 32;
+    return (int32_t)((hi * (uint64_t)n_levels) >> 32);
+}

@@ -571,3 +571,82 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
     if (err) return fail(ctx, err, "dagrt_bound: a tile copy did not complete in time");
     return DAGRT_OK;
 }
+
+// ------------------------------------------------------------------ search
+extern "C" int dagrt_search(dagrt_batch *b, const dagrt_search_cfg *cfg, int64_t *out_bound, int64_t *best_bound,
+                            int32_t *best_cand, uint8_t *best_m, uint32_t flags) {
+    if (!b) return DAGRT_E_INVAL;
+    dagrt_ctx *ctx = b->ctx;
+    if (!cfg) return fail(ctx, DAGRT_E_INVAL, "dagrt_search: cfg is NULL");
+    if (flags & ~DAGRT_PTR_DEVICE) return fail(ctx, DAGRT_E_INVAL, "dagrt_search: unknown flags 0x%x", flags);
+    if (cfg->n_variants < 1 || cfg->n_variants > kMaxVariantsPerCall || !cfg->variant_ids)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_search: n_variants must be in [1, %d]", kMaxVariantsPerCall);
+    if (cfg->n_alloc < 1 || (int64_t)cfg->n_variants * cfg->n_alloc > (1 << 20))
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_search: need 1 <= n_alloc and n_variants * n_alloc <= 2^20");
+    if (cfg->n_levels < 1 || cfg->n_levels > 16 || !cfg->levels)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_search: n_levels must be in [1, 16]");
+    for (int i = 0; i < cfg->n_levels; i++)
+        if (cfg->levels[i] < 1) return fail(ctx, DAGRT_E_INVAL, "dagrt_search: level %d is 0", i);
+    if (b->n_dags >= (1 << 24)) return fail(ctx, DAGRT_E_INVAL, "dagrt_search: too many DAGs");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    BoundArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.n_dags = b->n_dags;
+    a.node_off = b->node_off;
+    a.M = b->M;
+    a.n_variants = cfg->n_variants;
+    a.n_alloc = cfg->n_alloc;
+    a.stride = 16;
+    a.err = b->err;
+    a.gen = 1;
+    a.seed = cfg->seed;
+    a.n_levels = cfg->n_levels;
+    for (int i = 0; i < 16; i++) a.levels[i] = i < cfg->n_levels ? cfg->levels[i] : cfg->levels[0];
+    for (int i = 0; i < cfg->n_variants; i++) {
+        const int v = cfg->variant_ids[i];
+        if (v < 0 || v >= DAGRT_N_VARIANTS || !b->plan[v].valid)
+            return fail(ctx, DAGRT_E_INVAL, "dagrt_search: variant %d was not scheduled on this batch", v);
+        a.plan[i] = b->plan[v].rows;
+        a.nrows[i] = b->plan[v].nrows;
+        a.pflag[i] = b->plan[v].pflag;
+        a.status[i] = b->plan[v].status;
+    }
+    const bool dev = (flags & DAGRT_PTR_DEVICE) != 0;
+    const size_t nd = b->n_dags;
+    const int64_t n_cand = (int64_t)cfg->n_variants * cfg->n_alloc;
+    const size_t out_bytes = nd * (size_t)n_cand * 8, m_bytes = (size_t)(2 * b->total_nodes);
+    if (dev) {
+        a.out = out_bound;
+        a.best_bound = best_bound;
+        a.best_cand = best_cand;
+        a.best_m = best_m;
+    } else {
+        const size_t need = (out_bound ? (out_bytes + 255) / 256 * 256 : 0) + (8 * nd + 255) / 256 * 256 +
+                            (4 * nd + 255) / 256 * 256 + (best_m ? (m_bytes + 255) / 256 * 256 : 0) + 256;
+        int rc = ensure_tmp(b, need);
+        if (rc) return rc;
+        char *t = (char *)b->tmp;
+        auto take = [&](size_t bytes) {
+            char *p = t;
+            t += (bytes + 255) / 256 * 256;
+            return (void *)p;
+        };
+        a.out = out_bound ? (int64_t *)take(out_bytes) : nullptr;
+        a.best_bound = (int64_t *)take(8 * nd);
+        a.best_cand = (int32_t *)take(4 * nd);
+        a.best_m = best_m ? (uint8_t *)take(m_bytes) : nullptr;
+        if (best_m && m_bytes) CK(cudaMemsetAsync(a.best_m, 0, m_bytes, ctx->stream), "clear best_m");
+    }
+    CK(bound_launch(a, ctx->n_sm, ctx->stream), "launch search kernel");
+    if (nd) ctx->launches++;
+    if (dev) return DAGRT_OK;
+    if (out_bound && out_bytes) CK(cudaMemcpyAsync(out_bound, a.out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy bounds");
+    if (best_bound && nd) CK(cudaMemcpyAsync(best_bound, a.best_bound, 8 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy best");
+    if (best_cand && nd) CK(cudaMemcpyAsync(best_cand, a.best_cand, 4 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy best");
+    if (best_m && m_bytes) CK(cudaMemcpyAsync(best_m, a.best_m, m_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy best_m");
+    int32_t err = 0;
+    CK(cudaMemcpyAsync(&err, b->err, sizeof err, cudaMemcpyDeviceToHost, ctx->stream), "copy error word");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    if (err) return fail(ctx, err, "dagrt_search: a tile copy did not complete in time");
+    return DAGRT_OK;
+}

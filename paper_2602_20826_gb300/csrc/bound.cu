@@ -10,9 +10,10 @@
 // run of T * cand_stride bytes) and the T plan rows of every variant in the call -- stream
 // from global to shared memory with TMA bulk copies into two stages that complete on
 // mbarriers, so the loads of tile i+1 overlap the evaluation of tile i. Each thread owns
-// 4 adjacent candidates of one variant (one 32-bit shared load per row) or 1 candidate
-// when variants are not 4-aligned, keeps their running group states, and the argmin over
-// the DAG's candidates is reduced with warp shuffles and shared memory in the same kernel.
+// 1, 2 or 4 adjacent candidates of one variant (one shared load per row), chosen so that a
+// warp covers a single variant when possible, keeps their running group states, and the
+// argmin over the DAG's candidates is reduced with warp shuffles and shared memory in the
+// same kernel.
 #include "bound.cuh"
 #include "dagrt_internal.cuh"
 
@@ -86,18 +87,20 @@ __host__ __device__ inline TileLayout tile_layout(int T, int64_t stride, int nv)
     return t;
 }
 
-template <int CPT>
+template <int CPT, bool GEN>
 __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int T) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_abort;
     __shared__ int64_t s_bb[kBoundMaxThreads / 32];
     __shared__ int32_t s_bc[kBoundMaxThreads / 32];
+    __shared__ uint8_t s_lev[16];
     const int nv = a.n_variants;
     const int n_cand = nv * a.n_alloc;
     const uint32_t M = (uint32_t)a.M;
-    const int64_t stride = a.stride;
+    const int64_t stride = GEN ? 0 : a.stride;  // generated candidates stream plan rows only
     const TileLayout L = tile_layout(T, stride, nv);
+    if (GEN && threadIdx.x < 16) s_lev[threadIdx.x] = a.levels[threadIdx.x];
     unsigned char *stage[2] = {sm, sm + L.stage_bytes};
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -128,10 +131,10 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
             const int my_rows = valid ? a.nrows[vi][d] : 0;
             const bool fit = valid && (a.pflag[vi][d] & 1);
             uint64_t bound[CPT];
-            uint64_t gmax[CPT], gsum[CPT];
-            uint32_t gm[CPT];
+            uint64_t gmax[CPT], gsum[CPT];              // group state, 64-bit path
+            uint32_t gmax32[CPT], gsum32[CPT], gm[CPT];  // group state, 32-bit path; SM sum
 #pragma unroll
-            for (int i = 0; i < CPT; i++) bound[i] = gmax[i] = gsum[i] = gm[i] = 0;
+            for (int i = 0; i < CPT; i++) bound[i] = gmax[i] = gsum[i] = gmax32[i] = gsum32[i] = gm[i] = 0;
 
             // tile i of the DAG into stage i & 1
             auto issue = [&](int i) {
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
                 const uint32_t cb = (uint32_t)(rn * stride);
                 issued[s]++;
                 mbar_expect_tx(&bar[s], cb + (uint32_t)(nv * rn * 16));
-                bulk_g2s(stage[s], a.m_alloc + (rbase + r0) * stride, cb, &bar[s]);
+                if (!GEN) bulk_g2s(stage[s], a.m_alloc + (rbase + r0) * stride, cb, &bar[s]);
                 for (int v = 0; v < nv; v++)
                     bulk_g2s(stage[s] + L.cand_bytes + (int64_t)v * T * 16, a.plan[v] + rbase + r0,
                              (uint32_t)(rn * 16), &bar[s]);
@@ -165,49 +168,73 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
                 for (int rr = 0; rr < rn; rr++) {
                     const uint4 x = pl[rr];
                     const uint32_t k = (x.z >> 16) & 0xffu, m0 = x.z & 0xffffu;
+                    const bool last = (x.z >> 24) != 0;
                     uint32_t m4;
-                    if (CPT == 4) m4 = *(const uint32_t *)(cbuf + rr * stride);
-                    else m4 = cbuf[rr * stride];
+                    if (GEN) {
+                        m4 = 0;
+#pragma unroll
+                        for (int q = 0; q < CPT; q++) {
+                            const int cq = c + q;
+                            if (cq % a.n_alloc != 0)
+                                m4 |= (uint32_t)s_lev[gen_level(a.seed, d, cq, r0 + rr, a.n_levels)] << (8 * q);
+                        }
+                    } else if (CPT == 4) {
+                        m4 = *(const uint32_t *)(cbuf + rr * stride);
+                    } else if (CPT == 2) {
+                        m4 = *(const uint16_t *)(cbuf + rr * stride);
+                    } else {
+                        m4 = cbuf[rr * stride];
+                    }
                     if (fit) {
+                        // C for m = 2^l <= M, 32-bit exact for this DAG:
+                        // ceil(x (64m - k(m-1)) / 64m) = ((x(64-k) + 64) << l + x k - 1) >> (l + 6)
                         const uint32_t A1 = x.x * (64u - k) + 64u, B1 = x.x * k - 1u;
+                        uint32_t cc[CPT];
+                        bool slow = false;
 #pragma unroll
                         for (int q = 0; q < CPT; q++) {
                             const uint32_t m = (m4 >> (8 * q)) & 0xffu;
-                            uint32_t cc, mm;
-                            if (m == 0) {
-                                cc = x.y;
-                                mm = m0;
-                            } else if ((m & (m - 1)) == 0 && m <= M) {
-                                // C = ceil(x (64m - k(m-1)) / 64m) for m = 2^l, 32-bit exact here:
-                                // ((x(64-k) + 64) << l + x k - 1) >> (l + 6)
-                                const int l = 31 - __clz(m);
-                                cc = ((A1 << l) + B1) >> (l + 6);
-                                mm = m;
-                            } else {
-                                cc = (uint32_t)exec_time(x.x, k, m, M);
-                                mm = m;
+                            const int l = 31 - __clz(m | (m == 0));
+                            cc[q] = m ? ((A1 << l) + B1) >> (l + 6) : x.y;
+                            slow |= ((m & (m - 1)) != 0) | (m > M);
+                        }
+                        if (slow) {  // an allocation that is not a power of two, or above M
+#pragma unroll
+                            for (int q = 0; q < CPT; q++) {
+                                const uint32_t m = (m4 >> (8 * q)) & 0xffu;
+                                if (((m & (m - 1)) != 0) | (m > M)) cc[q] = (uint32_t)exec_time(x.x, k, m, M);
                             }
-                            gmax[q] = cc > gmax[q] ? cc : gmax[q];
-                            gsum[q] += cc;
-                            gm[q] += mm;
+                        }
+#pragma unroll
+                        for (int q = 0; q < CPT; q++) {
+                            const uint32_t m = (m4 >> (8 * q)) & 0xffu;
+                            gmax32[q] = cc[q] > gmax32[q] ? cc[q] : gmax32[q];
+                            gsum32[q] += cc[q];
+                            gm[q] += m ? m : m0;
+                        }
+                        if (last) {
+#pragma unroll
+                            for (int q = 0; q < CPT; q++) {
+                                bound[q] += gm[q] <= M ? gmax32[q] : gsum32[q];
+                                gmax32[q] = gsum32[q] = gm[q] = 0;
+                            }
                         }
                     } else {
 #pragma unroll
                         for (int q = 0; q < CPT; q++) {
                             const uint32_t m = (m4 >> (8 * q)) & 0xffu;
-                            const uint32_t mm = m ? m : m0;
-                            const uint64_t cc = m ? exec_time(x.x, k, m, M) : (uint64_t)x.y;
-                            gmax[q] = cc > gmax[q] ? cc : gmax[q];
-                            gsum[q] += cc;
-                            gm[q] += mm;
+                            const uint64_t ccw = m ? exec_time(x.x, k, m, M) : (uint64_t)x.y;
+                            gmax[q] = ccw > gmax[q] ? ccw : gmax[q];
+                            gsum[q] += ccw;
+                            gm[q] += m ? m : m0;
                         }
-                    }
-                    if (x.z >> 24) {
+                        if (last) {
 #pragma unroll
-                        for (int q = 0; q < CPT; q++) {
-                            bound[q] += gm[q] <= M ? gmax[q] : gsum[q];
-                            gmax[q] = gsum[q] = 0;
-                            gm[q] = 0;
+                            for (int q = 0; q < CPT; q++) {
+                                bound[q] += gm[q] <= M ? gmax[q] : gsum[q];
+                                gmax[q] = gsum[q] = 0;
+                                gm[q] = 0;
+                            }
                         }
                     }
                 }
@@ -243,6 +270,14 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
                 for (int w = 1; w < (int)(blockDim.x >> 5); w++) better(best_b, best_c, s_bb[w], s_bc[w]);
                 if (a.best_bound) a.best_bound[d] = best_c < 0 ? -1 : best_b;
                 if (a.best_cand) a.best_cand[d] = best_c;
+                s_bc[0] = best_c;
+            }
+            __syncthreads();
+            if (GEN && a.best_m && s_bc[0] >= 0) {  // the winning allocation, row by row
+                const int wc = s_bc[0], wv = wc / a.n_alloc;
+                const int rows = a.nrows[wv][d];
+                for (int r = tid; r < rows; r += blockDim.x)
+                    a.best_m[rbase + r] = wc % a.n_alloc == 0 ? 0 : s_lev[gen_level(a.seed, d, wc, r, a.n_levels)];
             }
             __syncthreads();
         }
@@ -259,33 +294,33 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
 cudaError_t bound_launch(const BoundArgs &a, int n_sm, cudaStream_t st) {
     if (a.n_dags == 0) return cudaSuccess;
     const int n_cand = a.n_variants * a.n_alloc;
-    // 4 adjacent candidates never straddle two variants when n_alloc % 4 == 0
-    const int cpt = a.n_alloc % 4 == 0 ? 4 : 1;
+    // candidates per thread: a warp should cover candidates of one variant only (uniform
+    // group boundaries), and a thread's candidates must never straddle two variants
+    int cpt = 1;
+    for (int q : {4, 2})
+        if (a.n_alloc % (32 * q) == 0) { cpt = q; break; }
+    if (cpt == 1 && a.n_alloc % 32 != 0) cpt = a.n_alloc % 4 == 0 ? 4 : (a.n_alloc % 2 == 0 ? 2 : 1);
     int threads = (n_cand + cpt - 1) / cpt;
     threads = (threads + 31) / 32 * 32;
     if (threads > kBoundMaxThreads) threads = kBoundMaxThreads;
-    // rows per tile: about 8 KB of candidate bytes per stage, at least 4
-    int T = (int)(8192 / (a.stride + 16ll * a.n_variants));
+    // rows per tile: about 8 KB of candidate bytes (plan rows when generating) per stage
+    int T = (int)(8192 / ((a.gen ? 0 : a.stride) + 16ll * a.n_variants));
     if (T < 1) T = 1;
     if (T > 128) T = 128;
-    const TileLayout L = tile_layout(T, a.stride, a.n_variants);
+    const TileLayout L = tile_layout(T, a.gen ? 0 : a.stride, a.n_variants);
     const int64_t smem = 2 * L.stage_bytes;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e;
+    void (*kern)(BoundArgs, int) =
+        a.gen ? (cpt == 4 ? k_bound_tma<4, true> : cpt == 2 ? k_bound_tma<2, true> : k_bound_tma<1, true>)
+              : (cpt == 4 ? k_bound_tma<4, false> : cpt == 2 ? k_bound_tma<2, false> : k_bound_tma<1, false>);
     int per_sm = 0;
-    if (cpt == 4) {
-        e = cudaFuncSetAttribute(k_bound_tma<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bound_tma<4>, threads, smem);
-    } else {
-        e = cudaFuncSetAttribute(k_bound_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bound_tma<1>, threads, smem);
-    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int grid = a.n_dags;
     if (grid > per_sm * n_sm) grid = per_sm * n_sm;
-    if (cpt == 4) k_bound_tma<4><<<grid, threads, smem, st>>>(a, T);
-    else k_bound_tma<1><<<grid, threads, smem, st>>>(a, T);
+    kern<<<grid, threads, smem, st>>>(a, T);
     return cudaGetLastError();
 }
 

@@ -436,3 +436,27 @@ def test_validation_error_codes():
     rc, r = oracle.schedule(np.array([0], np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64),
                             np.zeros(0, np.uint8), 4)
     assert rc == oracle.OK and r["bound"] == 0 and r["n_groups"] == 0
+
+
+# ------------------------------------------------------- candidate generator
+
+def test_splitmix64_published_outputs():
+    """SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) seeded with 0 yields
+    0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F as its first outputs; the
+    generator advances the state by the golden gamma before mixing."""
+    g = 0x9E3779B97F4A7C15
+    assert oracle.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert oracle.splitmix64(g) == 0x6E789E6AA1B965F4
+    assert oracle.splitmix64(2 * g) == 0x06C45D188009454F
+
+
+def test_generated_levels_are_uniform_and_keep_candidate_zero():
+    levels = [1, 2, 4, 8, 16, 32]
+    counts = np.zeros(len(levels), int)
+    for c in range(1, 200):
+        a = oracle.generated_allocation(7, 3, c, 50, levels, 200)
+        for x in a:
+            counts[levels.index(int(x))] += 1
+    assert counts.min() > 0.9 * counts.mean() and counts.max() < 1.1 * counts.mean()
+    assert not oracle.generated_allocation(7, 3, 0, 50, levels, 200).any()
+    assert not oracle.generated_allocation(7, 3, 400, 50, levels, 200).any()
