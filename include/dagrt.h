@@ -233,6 +233,75 @@ int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_
                            const uint8_t *k64, int32_t M, int32_t variant, int64_t *bound,
                            int32_t *status, void *cuda_stream);
 
+/* ---------------------------------------------------------------- learned proposer
+ * The paper gives the bound of one allocation (Eq.1, Lemma 1, Theorem 1) but no way to
+ * choose among the many allocations of a DAG beyond the Eq.5 heuristic of Alg.2. The
+ * proposer is an extension of the bound's evaluation, not a step of the paper: a
+ * message-passing network scores, for every kernel, which SM level of a fixed level list
+ * it should get; the k most likely joint assignments (and the paper's own allocation) are
+ * then evaluated exactly on the paper schedule's structure (Alg.2 groups and segments,
+ * Theorem 1) and the smallest bound wins. The exact check makes every returned bound a
+ * true Theorem 1 bound of a valid allocation, whatever the network's quality.
+ *
+ * Network: x_i (8 features, zero-padded to 16): log2 C^_i / 32, k_i / 64,
+ * log2(1 + indegree) / 8, log2(1 + outdegree) / 8, level_i / depth (Alg.1 levels),
+ * W^anc_i / sum C^ (the ancestor weight Alg.1 orders by), log2 m_i / 12 (the paper
+ * schedule's m_i, Eq.5), 1. Three layers h' = ReLU([h | mean_pred h | mean_succ h] W + b)
+ * with hidden width 128 (W: [3*16 x 128] then [384 x 128]), then a head h3 Wh + bh to one
+ * logit per level (Wh: [128 x 16], unused levels ignored). Activations and GEMM operands
+ * are bf16 with fp32 accumulation; parameters are fp32 in the order W1, b1, W2, b2, W3,
+ * b3, Wh, bh (row-major, input index first), dagrt_model_n_params() floats in all.
+ * Training minimises the mean softmax cross-entropy over labelled kernels with Adam
+ * (beta 0.9/0.999, eps 1e-8). Reductions over nodes run in a fixed order, so results
+ * repeat bit for bit on one GPU. */
+typedef struct dagrt_model dagrt_model;
+
+/* Number of fp32 parameters. */
+int64_t dagrt_model_n_params(void);
+
+/* New model on ctx's device: levels[0..n_levels) are the SM counts a kernel may be given
+ * (1 <= n_levels <= 16, each >= 1; levels above M are allowed and clamp like any m in
+ * Eq.1's ceil(m/M) term). Weights are uniform in +-sqrt(6/fan_in) from the SplitMix64
+ * stream starting at `seed`; biases are 0. Returns DAGRT_E_INVAL or DAGRT_E_DEVICE on
+ * failure, with *out = NULL. */
+int dagrt_model_create(dagrt_ctx *ctx, int32_t n_levels, const uint8_t *levels, uint64_t seed,
+                       dagrt_model **out);
+void dagrt_model_free(dagrt_model *model);
+
+/* Host copy of the parameters out (get != NULL) and/or in (set != NULL; set is applied
+ * first), dagrt_model_n_params() floats each. Synchronous. */
+int dagrt_model_params(dagrt_model *model, float *get, const float *set);
+
+/* Logits of every kernel of the batch: logits[(node_off[d] + i) * n_levels + l]. The first
+ * call on a batch also runs the paper schedule (variant 0) for the features. */
+int dagrt_model_logits(dagrt_batch *batch, dagrt_model *model, float *logits, uint32_t flags);
+
+/* Mean cross-entropy over the labelled kernels and its gradient. labels[total_nodes] (host)
+ * holds each kernel's level index, or -1 for no label. grads (host, n_params floats, may be
+ * NULL) receives dLoss/dparams; *loss (may be NULL) the loss. Synchronous. */
+int dagrt_model_grad(dagrt_batch *batch, dagrt_model *model, const int8_t *labels, float *grads,
+                     float *loss);
+
+/* dagrt_model_grad followed by one Adam step with learning rate lr. Synchronous. */
+int dagrt_train_step(dagrt_batch *batch, dagrt_model *model, const int8_t *labels, float lr,
+                     float *loss);
+
+/* Proposals and their exact check, per DAG: candidate 0 is the paper's allocation (Alg.2's
+ * m_i), candidates 1..k (1 <= k <= 16) the k most likely level assignments under the
+ * model, most likely first (kernel i's level applies to every plan row of i, its segments
+ * included). Each is evaluated on the paper schedule's structure exactly as dagrt_bound
+ * does. Outputs (any may be NULL):
+ *   out_bound[d * (k+1) + c]    bound of candidate c of DAG d;
+ *   cand_m[(2 * node_off[d] + r) * (k+1) + c]   candidate c's SMs for plan row r
+ *                               (0 in column 0 = the schedule's own m; rows >= n_rows unset);
+ *   best_bound[d], best_cand[d] the smallest bound and its candidate (lowest index on ties,
+ *                               so the paper's allocation wins ties);
+ *   best_m[2 * node_off[d] + r] the winning allocation of plan row r.
+ * Host outputs are synchronous; with DAGRT_PTR_DEVICE the call only enqueues work. */
+int dagrt_propose(dagrt_batch *batch, dagrt_model *model, int32_t k, int64_t *out_bound,
+                  uint8_t *cand_m, int64_t *best_bound, int32_t *best_cand, uint8_t *best_m,
+                  uint32_t flags);
+
 #ifdef __cplusplus
 }
 #endif

@@ -229,7 +229,7 @@ int or_schedule_dag(int32_t V, const int32_t *row_ptr, const int32_t *col,
             if (bit_get(&anc[(int64_t)v * nw], u)) W[v] += wcet[u];
     }
 
-    /* --- Alg.1 line 1: join nodes (>= 2 predecessors) ordered by W^anc ------- */
+    /* --- Alg.1, first step: join nodes (>= 2 predecessors) ordered by W^anc ------- */
     int32_t *theta = calloc(V, sizeof *theta);
     int32_t N = 0;
     for (int32_t v = 0; v < V; v++)
@@ -237,7 +237,7 @@ int or_schedule_dag(int32_t V, const int32_t *row_ptr, const int32_t *col,
     g_key_w = W;
     qsort(theta, N, sizeof *theta, cmp_w_asc_id_asc);
 
-    /* --- Alg.1 lines 2-6, Eq.3: B_k = ance(theta_k) minus earlier blocks; the
+    /* --- Alg.1, block step, Eq.3: B_k = ance(theta_k) minus earlier blocks; the
      *     remaining nodes form the residual block B_{N+1} (index N here) ------ */
     int32_t *block_of = malloc(V * sizeof *block_of);
     for (int32_t v = 0; v < V; v++) block_of[v] = -1;
@@ -249,7 +249,7 @@ int or_schedule_dag(int32_t V, const int32_t *row_ptr, const int32_t *col,
     for (int32_t u = 0; u < V; u++)
         if (block_of[u] < 0) block_of[u] = N;
 
-    /* --- Alg.1 lines 7-17: per block, local complete paths (Eq.4) and balanced
+    /* --- Alg.1, path step: per block, local complete paths (Eq.4) and balanced
      *     groups built from their heads ---------------------------------------- */
     int32_t *group_of = malloc(V * sizeof *group_of);
     for (int32_t v = 0; v < V; v++) group_of[v] = -1;
@@ -409,7 +409,7 @@ int or_schedule_dag(int32_t V, const int32_t *row_ptr, const int32_t *col,
             }
         }
 
-        /* Alg.2 lines 7-17: launch parallel nodes, segment when one does not fit */
+        /* Alg.2, parallel step: launch parallel nodes, segment when one does not fit */
         int32_t nl = 0;
         for (int32_t q = 0; q < nq && variant != OR_VAR_NOPARA; q++) {
             int32_t u = Q[q];

@@ -12,6 +12,7 @@
 
 #include "dagrt.h"
 #include "bound.cuh"
+#include "gnn.cuh"
 #include "sched.cuh"
 
 using namespace dagrt;
@@ -49,7 +50,24 @@ struct dagrt_ctx {
     int n_batches = 0;
     int64_t launches = 0;
     DevicePool pool;
+    // side streams: the scheduler's size-class kernels run concurrently, forked from and
+    // joined back into `stream` with events
+    static constexpr int kSide = 5;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
+    bool side_ready = false;
 };
+
+static cudaError_t ensure_side_streams(dagrt_ctx *c) {
+    if (c->side_ready) return cudaSuccess;
+    cudaError_t e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    for (int i = 0; i < dagrt_ctx::kSide && e == cudaSuccess; i++) {
+        e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) c->side_ready = true;
+    return e;
+}
 
 namespace {
 
@@ -89,6 +107,18 @@ struct dagrt_batch {
     // scratch for candidate evaluation
     void *tmp = nullptr;
     size_t tmp_cap = 0;
+    // learned proposer: message-passing graph, features, activations (allocated on first use)
+    struct Gnn {
+        bool graph = false, train = false;
+        int32_t *pred_off, *pred_idx, *succ_off, *succ_idx, *cursor, *level, *m;
+        int64_t *wanc;
+        uint16_t *x, *h[3];
+        float *logits, *dlogits, *dh[3], *da, *loss_part;
+        int8_t *labels;
+        uint8_t *best_level, *cand;
+        int32_t *cbest;
+        int64_t *bbest;
+    } gnn;
 };
 
 static int fail(dagrt_ctx *ctx, int code, const char *fmt, ...) {
@@ -172,6 +202,13 @@ void dagrt_destroy(dagrt_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ctx->pool.release_all();
+    if (ctx->side_ready) {
+        for (int i = 0; i < dagrt_ctx::kSide; i++) {
+            cudaStreamDestroy(ctx->side[i]);
+            cudaEventDestroy(ctx->join[i]);
+        }
+        cudaEventDestroy(ctx->fork);
+    }
     delete ctx;
 }
 
@@ -453,27 +490,32 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
     a.o = dv;
     if (nd > 0) {
         CK(cudaMemsetAsync(b->counters, 0, 8 * sizeof(int32_t), ctx->stream), "reset counters");
-        for (int c = 0; c < kNumWarpClasses; c++) {
+        CK(ensure_side_streams(ctx), "create side streams");
+        // size classes run concurrently: fork from the context stream, join back into it
+        CK(cudaEventRecord(ctx->fork, ctx->stream), "record fork");
+        int used[dagrt_ctx::kSide], nused = 0;
+        for (int c = 0; c <= kNumWarpClasses; c++) {
             const int n = b->class_off[c + 1] - b->class_off[c];
             if (n == 0) continue;
+            cudaStream_t st = ctx->side[c];
+            CK(cudaStreamWaitEvent(st, ctx->fork, 0), "fork");
             a.list = b->lists + b->class_off[c];
             a.n_list = n;
             a.counter = b->counters + c;
-            CK(sched_launch_warp(kWarpClassCap[c], a, ctx->n_sm, ctx->stream), "launch scheduler (warp teams)");
+            if (c < kNumWarpClasses) {
+                CK(sched_launch_warp(kWarpClassCap[c], a, ctx->n_sm, st), "launch scheduler (warp teams)");
+            } else {
+                a.gws = b->gws;
+                a.gws_stride = b->gws_stride;
+                a.vcap = b->big_vcap;
+                a.ecap = b->big_ecap;
+                CK(sched_launch_cta(a, b->big_grid, st), "launch scheduler (CTA teams)");
+            }
             ctx->launches++;
+            CK(cudaEventRecord(ctx->join[c], st), "record join");
+            used[nused++] = c;
         }
-        const int nbig = b->class_off[kNumWarpClasses + 1] - b->class_off[kNumWarpClasses];
-        if (nbig > 0) {
-            a.list = b->lists + b->class_off[kNumWarpClasses];
-            a.n_list = nbig;
-            a.counter = b->counters + kNumWarpClasses;
-            a.gws = b->gws;
-            a.gws_stride = b->gws_stride;
-            a.vcap = b->big_vcap;
-            a.ecap = b->big_ecap;
-            CK(sched_launch_cta(a, b->big_grid, ctx->stream), "launch scheduler (CTA teams)");
-            ctx->launches++;
-        }
+        for (int i = 0; i < nused; i++) CK(cudaStreamWaitEvent(ctx->stream, ctx->join[used[i]], 0), "join");
     }
     p.valid = true;
     if (dev) return DAGRT_OK;
@@ -648,5 +690,342 @@ extern "C" int dagrt_search(dagrt_batch *b, const dagrt_search_cfg *cfg, int64_t
     CK(cudaMemcpyAsync(&err, b->err, sizeof err, cudaMemcpyDeviceToHost, ctx->stream), "copy error word");
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     if (err) return fail(ctx, err, "dagrt_search: a tile copy did not complete in time");
+    return DAGRT_OK;
+}
+
+// ------------------------------------------------------------------ learned proposer
+// proposal buffer: column 0 = the paper's allocation, columns 1..k = the k best assignments
+constexpr int64_t kPropStride = 32;
+
+struct dagrt_model {
+    dagrt_ctx *ctx = nullptr;
+    int32_t L = 0;
+    uint8_t levels[kMaxLevels] = {0};
+    uint8_t *d_levels = nullptr;
+    float *p = nullptr, *m = nullptr, *v = nullptr, *part = nullptr;
+    int n_parts = 0, step = 0;
+    uint16_t *wt[3] = {}, *wb[3] = {};
+    std::vector<std::pair<void *, size_t>> owned;
+};
+
+namespace {
+
+template <class T>
+cudaError_t model_alloc(dagrt_model *md, T **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = md->ctx->pool.get(&q, (n ? n : 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        *p = (T *)q;
+        md->owned.emplace_back(q, (n ? n : 1) * sizeof(T));
+    }
+    return e;
+}
+
+GnnGraph graph_of(dagrt_batch *b) {
+    GnnGraph g;
+    g.n_nodes = b->total_nodes;
+    g.n_edges = b->total_edges;
+    g.pred_off = b->gnn.pred_off;
+    g.pred_idx = b->gnn.pred_idx;
+    g.succ_off = b->gnn.succ_off;
+    g.succ_idx = b->gnn.succ_idx;
+    return g;
+}
+
+}  // namespace
+
+// variant-0 schedule (plan, levels, W^anc, m), message-passing graph and node features
+static int gnn_prepare(dagrt_batch *b, bool train) {
+    dagrt_ctx *ctx = b->ctx;
+    auto &G = b->gnn;
+    const size_t N = (size_t)b->total_nodes, E = (size_t)b->total_edges;
+    cudaError_t e;
+    if (!G.graph) {
+        if ((e = batch_alloc(b, &G.pred_off, N + 1)) != cudaSuccess || (e = batch_alloc(b, &G.succ_off, N + 1)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.pred_idx, E)) != cudaSuccess || (e = batch_alloc(b, &G.succ_idx, E)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.cursor, N)) != cudaSuccess || (e = batch_alloc(b, &G.level, N)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.m, N)) != cudaSuccess || (e = batch_alloc(b, &G.wanc, N)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.x, N * kFeat)) != cudaSuccess || (e = batch_alloc(b, &G.h[0], N * kHidden)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.h[1], N * kHidden)) != cudaSuccess || (e = batch_alloc(b, &G.h[2], N * kHidden)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.logits, N * kMaxLevels)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.best_level, N)) != cudaSuccess || (e = batch_alloc(b, &G.cand, 2 * N * kPropStride)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.cbest, b->n_dags)) != cudaSuccess || (e = batch_alloc(b, &G.bbest, b->n_dags)) != cudaSuccess)
+            return cuda_fail(ctx, e, "allocate proposer state");
+        dagrt_schedule_out o;
+        std::memset(&o, 0, sizeof o);
+        o.level = G.level;
+        o.wanc = G.wanc;
+        o.m = G.m;
+        int rc = dagrt_schedule(b, DAGRT_VAR_PAPER, &o, DAGRT_PTR_DEVICE);
+        if (rc) return rc;
+        CK(gnn_build_graph(b->n_dags, b->node_off, b->edge_off, b->row_ptr, b->col, G.pred_off, G.pred_idx, G.succ_off,
+                           G.succ_idx, G.cursor, ctx->n_sm, ctx->stream), "build message-passing graph");
+        CK(gnn_features(b->n_dags, b->node_off, b->wcet, b->k64, G.level, G.wanc, G.m, graph_of(b), G.x, ctx->n_sm,
+                        ctx->stream), "node features");
+        ctx->launches += 3;
+        G.graph = true;
+    }
+    if (train && !G.train) {
+        if ((e = batch_alloc(b, &G.dlogits, N * kMaxLevels)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.dh[0], N * kHidden)) != cudaSuccess || (e = batch_alloc(b, &G.dh[1], N * kHidden)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.dh[2], N * kHidden)) != cudaSuccess || (e = batch_alloc(b, &G.da, N * 3 * kHidden)) != cudaSuccess ||
+            (e = batch_alloc(b, &G.labels, N)) != cudaSuccess || (e = batch_alloc(b, &G.loss_part, 1024)) != cudaSuccess)
+            return cuda_fail(ctx, e, "allocate training state");
+        G.train = true;
+    }
+    return DAGRT_OK;
+}
+
+static int gnn_forward(dagrt_batch *b, dagrt_model *md) {
+    dagrt_ctx *ctx = b->ctx;
+    auto &G = b->gnn;
+    const GnnGraph g = graph_of(b);
+    const int64_t boff[3] = {ParamLayout::b1, ParamLayout::b2, ParamLayout::b3};
+    const uint16_t *in = G.x;
+    for (int l = 0; l < 3; l++) {
+        CK(gnn_layer_fwd(l == 0 ? kFeat : kHidden, g, in, md->wt[l], md->p + boff[l], G.h[l], b->err, ctx->n_sm,
+                         ctx->stream), "layer forward");
+        in = G.h[l];
+    }
+    ctx->launches += 3;
+    return DAGRT_OK;
+}
+
+extern "C" int64_t dagrt_model_n_params(void) { return ParamLayout::total; }
+
+extern "C" int dagrt_model_create(dagrt_ctx *ctx, int32_t n_levels, const uint8_t *levels, uint64_t seed,
+                                  dagrt_model **out) {
+    if (!ctx) return DAGRT_E_INVAL;
+    if (!out) return fail(ctx, DAGRT_E_INVAL, "dagrt_model_create: out is NULL");
+    *out = nullptr;
+    if (n_levels < 1 || n_levels > kMaxLevels || !levels)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_model_create: n_levels must be in [1, %d]", kMaxLevels);
+    for (int i = 0; i < n_levels; i++)
+        if (levels[i] < 1) return fail(ctx, DAGRT_E_INVAL, "dagrt_model_create: level %d is 0", i);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    dagrt_model *md = new dagrt_model();
+    md->ctx = ctx;
+    md->L = n_levels;
+    for (int i = 0; i < n_levels; i++) md->levels[i] = levels[i];
+    md->n_parts = ctx->n_sm;
+    const int64_t n = ParamLayout::total;
+    cudaError_t e;
+    auto bail = [&](int code) {
+        for (auto &pb : md->owned) ctx->pool.put(pb.first, pb.second);
+        delete md;
+        return code;
+    };
+    if ((e = model_alloc(md, &md->p, n)) != cudaSuccess || (e = model_alloc(md, &md->m, n)) != cudaSuccess ||
+        (e = model_alloc(md, &md->v, n)) != cudaSuccess || (e = model_alloc(md, &md->part, (size_t)n * md->n_parts)) != cudaSuccess ||
+        (e = model_alloc(md, &md->d_levels, kMaxLevels)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "allocate model"));
+    const int Ks[3] = {3 * kFeat, 3 * kHidden, 3 * kHidden};
+    for (int l = 0; l < 3; l++)
+        if ((e = model_alloc(md, &md->wt[l], (size_t)Ks[l] * kHidden)) != cudaSuccess ||
+            (e = model_alloc(md, &md->wb[l], (size_t)Ks[l] * kHidden)) != cudaSuccess)
+            return bail(cuda_fail(ctx, e, "allocate model"));
+    // uniform(-a, a) weights with a = sqrt(6 / fan_in) from a SplitMix64 stream; zero biases
+    std::vector<float> h(n, 0.f);
+    uint64_t ctr = seed;
+    auto unif = [&]() { return (float)((splitmix64(ctr++) >> 40) * (1.0 / (double)(1ull << 24))) * 2.f - 1.f; };
+    const int64_t woff[4] = {ParamLayout::W1, ParamLayout::W2, ParamLayout::W3, ParamLayout::Wh};
+    const int fan_in[4] = {3 * kFeat, 3 * kHidden, 3 * kHidden, kHidden};
+    const int64_t wsz[4] = {3 * kFeat * kHidden, 3 * kHidden * kHidden, 3 * kHidden * kHidden, kHidden * kMaxLevels};
+    for (int l = 0; l < 4; l++) {
+        const float a = sqrtf(6.f / (float)fan_in[l]);
+        for (int64_t i = 0; i < wsz[l]; i++) h[woff[l] + i] = a * unif();
+    }
+    cudaStream_t st = ctx->stream;
+    if ((e = cudaMemcpyAsync(md->p, h.data(), n * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(md->m, 0, n * 4, st)) != cudaSuccess || (e = cudaMemsetAsync(md->v, 0, n * 4, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(md->d_levels, md->levels, kMaxLevels, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = gnn_refresh(md->p, md->wt, md->wb, st)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "initialise model"));
+    *out = md;
+    return DAGRT_OK;
+}
+
+extern "C" void dagrt_model_free(dagrt_model *md) {
+    if (!md) return;
+    cudaSetDevice(md->ctx->device);
+    cudaStreamSynchronize(md->ctx->stream);
+    for (auto &pb : md->owned) md->ctx->pool.put(pb.first, pb.second);
+    delete md;
+}
+
+extern "C" int dagrt_model_params(dagrt_model *md, float *get, const float *set) {
+    if (!md) return DAGRT_E_INVAL;
+    dagrt_ctx *ctx = md->ctx;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t bytes = ParamLayout::total * 4;
+    if (set) {
+        CK(cudaMemcpyAsync(md->p, set, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy params");
+        CK(gnn_refresh(md->p, md->wt, md->wb, ctx->stream), "refresh");
+    }
+    if (get) CK(cudaMemcpyAsync(get, md->p, bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy params");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return DAGRT_OK;
+}
+
+extern "C" int dagrt_model_logits(dagrt_batch *b, dagrt_model *md, float *logits, uint32_t flags) {
+    if (!b || !md) return DAGRT_E_INVAL;
+    dagrt_ctx *ctx = b->ctx;
+    if (md->ctx != ctx) return fail(ctx, DAGRT_E_INVAL, "dagrt_model_logits: model of another context");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = gnn_prepare(b, false);
+    if (rc) return rc;
+    if ((rc = gnn_forward(b, md))) return rc;
+    const GnnGraph g = graph_of(b);
+    float *dst = (flags & DAGRT_PTR_DEVICE) ? logits : b->gnn.logits;
+    CK(gnn_head(g, b->gnn.h[2], md->p + ParamLayout::Wh, md->p + ParamLayout::bh, md->L, nullptr, 0.f, dst, nullptr,
+                nullptr, nullptr, ctx->n_sm, ctx->stream), "head");
+    ctx->launches++;
+    if (flags & DAGRT_PTR_DEVICE) return DAGRT_OK;
+    if (logits && b->total_nodes)
+        CK(cudaMemcpyAsync(logits, dst, (size_t)b->total_nodes * md->L * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy logits");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return DAGRT_OK;
+}
+
+// loss and gradients for the labelled nodes (host labels, -1 = unlabelled) into the model's
+// per-CTA partial rows; *loss receives the mean cross-entropy
+static int gnn_grad(dagrt_batch *b, dagrt_model *md, const int8_t *labels, float *loss) {
+    dagrt_ctx *ctx = b->ctx;
+    auto &G = b->gnn;
+    int rc = gnn_prepare(b, true);
+    if (rc) return rc;
+    const size_t N = (size_t)b->total_nodes;
+    int64_t nl = 0;
+    for (size_t i = 0; i < N; i++) nl += labels[i] >= 0 && labels[i] < md->L;
+    const float scale = nl ? 1.f / (float)nl : 0.f;
+    cudaStream_t st = ctx->stream;
+    if (N) CK(cudaMemcpyAsync(G.labels, labels, N, cudaMemcpyHostToDevice, st), "copy labels");
+    if ((rc = gnn_forward(b, md))) return rc;
+    const GnnGraph g = graph_of(b);
+    CK(gnn_head(g, G.h[2], md->p + ParamLayout::Wh, md->p + ParamLayout::bh, md->L, G.labels, scale, G.logits, G.dlogits,
+                G.dh[2], G.loss_part, ctx->n_sm, st), "head");
+    CK(gnn_head_grad(g, G.h[2], G.dlogits, md->L, md->part, md->n_parts, st), "head gradient");
+    // layer 3 and 2: weight gradients, then the gradient of the layer input
+    for (int l = 2; l >= 1; l--) {
+        CK(gnn_layer_bwd_dw(kHidden, l, g, G.h[l - 1], G.h[l], G.dh[l], md->part, md->n_parts, b->err, st), "dW");
+        CK(gnn_layer_bwd_da(kHidden, g, G.h[l], G.dh[l], md->wb[l], G.da, b->err, ctx->n_sm, st), "dA");
+        CK(gnn_agg_bwd(kHidden, g, G.da, G.dh[l - 1], ctx->n_sm, st), "aggregation backward");
+    }
+    CK(gnn_layer_bwd_dw(kFeat, 0, g, G.x, G.h[0], G.dh[0], md->part, md->n_parts, b->err, st), "dW");
+    ctx->launches += 10;
+    std::vector<float> lp(ctx->n_sm);
+    CK(cudaMemcpyAsync(lp.data(), G.loss_part, 4 * ctx->n_sm, cudaMemcpyDeviceToHost, st), "copy loss");
+    int32_t err = 0;
+    CK(cudaMemcpyAsync(&err, b->err, sizeof err, cudaMemcpyDeviceToHost, st), "copy error word");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    if (err) return fail(ctx, err, "a tensor-core wait did not complete in time");
+    if (loss) {
+        double s = 0;
+        for (float x : lp) s += x;
+        *loss = (float)s;
+    }
+    return DAGRT_OK;
+}
+
+extern "C" int dagrt_model_grad(dagrt_batch *b, dagrt_model *md, const int8_t *labels, float *grads, float *loss) {
+    if (!b || !md || !labels) return b ? fail(b->ctx, DAGRT_E_INVAL, "dagrt_model_grad: NULL argument") : DAGRT_E_INVAL;
+    dagrt_ctx *ctx = b->ctx;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = gnn_grad(b, md, labels, loss);
+    if (rc) return rc;
+    if (grads) {  // fixed-order sum of the partial rows
+        const int64_t n = ParamLayout::total;
+        std::vector<float> part((size_t)n * md->n_parts);
+        CK(cudaMemcpy(part.data(), md->part, part.size() * 4, cudaMemcpyDeviceToHost), "copy partials");
+        for (int64_t i = 0; i < n; i++) {
+            float s = 0.f;
+            for (int c = 0; c < md->n_parts; c++) s += part[(size_t)c * n + i];
+            grads[i] = s;
+        }
+    }
+    return DAGRT_OK;
+}
+
+extern "C" int dagrt_train_step(dagrt_batch *b, dagrt_model *md, const int8_t *labels, float lr, float *loss) {
+    if (!b || !md || !labels) return b ? fail(b->ctx, DAGRT_E_INVAL, "dagrt_train_step: NULL argument") : DAGRT_E_INVAL;
+    dagrt_ctx *ctx = b->ctx;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = gnn_grad(b, md, labels, loss);
+    if (rc) return rc;
+    md->step++;
+    CK(gnn_adam(md->p, md->m, md->v, md->part, md->n_parts, ParamLayout::total, lr, 0.9f, 0.999f, 1e-8f, md->step,
+                ctx->stream), "Adam");
+    CK(gnn_refresh(md->p, md->wt, md->wb, ctx->stream), "refresh");
+    ctx->launches += 2;
+    return DAGRT_OK;
+}
+
+extern "C" int dagrt_propose(dagrt_batch *b, dagrt_model *md, int32_t k, int64_t *out_bound, uint8_t *cand_m,
+                             int64_t *best_bound, int32_t *best_cand, uint8_t *best_m, uint32_t flags) {
+    if (!b || !md) return b ? fail(b->ctx, DAGRT_E_INVAL, "dagrt_propose: model is NULL") : DAGRT_E_INVAL;
+    dagrt_ctx *ctx = b->ctx;
+    if (md->ctx != ctx) return fail(ctx, DAGRT_E_INVAL, "dagrt_propose: model of another context");
+    if (k < 1 || k > 16) return fail(ctx, DAGRT_E_INVAL, "dagrt_propose: k must be in [1, 16]");
+    if (flags & ~DAGRT_PTR_DEVICE) return fail(ctx, DAGRT_E_INVAL, "dagrt_propose: unknown flags 0x%x", flags);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = gnn_prepare(b, false);
+    if (rc) return rc;
+    if ((rc = gnn_forward(b, md))) return rc;
+    auto &G = b->gnn;
+    const GnnGraph g = graph_of(b);
+    cudaStream_t st = ctx->stream;
+    CK(gnn_head(g, G.h[2], md->p + ParamLayout::Wh, md->p + ParamLayout::bh, md->L, nullptr, 0.f, G.logits, nullptr,
+                nullptr, nullptr, ctx->n_sm, st), "head");
+    const Plan &pl = b->plan[DAGRT_VAR_PAPER];
+    CK(gnn_topk(b->n_dags, b->node_off, G.logits, md->L, md->d_levels, k, pl.rows, pl.nrows, G.best_level, G.cand,
+                kPropStride, ctx->n_sm, st), "top-k decode");
+    const bool dev = (flags & DAGRT_PTR_DEVICE) != 0;
+    const size_t nd = b->n_dags, nrow = (size_t)(2 * b->total_nodes), nc = (size_t)k + 1;
+    // host outputs are staged in the scratch block: [out_bound | best_m]
+    const size_t ob_bytes = (out_bound && !dev) ? (8 * nd * nc + 255) / 256 * 256 : 0;
+    const size_t bm_bytes = (best_m && !dev) ? (nrow + 255) / 256 * 256 : 0;
+    if (ob_bytes + bm_bytes) {
+        int rc2 = ensure_tmp(b, ob_bytes + bm_bytes);
+        if (rc2) return rc2;
+    }
+    // exact check of the candidates on the paper structure (Theorem 1, as dagrt_bound)
+    BoundArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.n_dags = b->n_dags;
+    a.node_off = b->node_off;
+    a.M = b->M;
+    a.n_variants = 1;
+    a.n_alloc = (int32_t)nc;
+    a.stride = kPropStride;
+    a.err = b->err;
+    a.plan[0] = pl.rows;
+    a.nrows[0] = pl.nrows;
+    a.pflag[0] = pl.pflag;
+    a.status[0] = pl.status;
+    a.m_alloc = G.cand;
+    a.out = out_bound ? (dev ? out_bound : (int64_t *)b->tmp) : nullptr;
+    a.best_bound = dev && best_bound ? best_bound : G.bbest;
+    a.best_cand = dev && best_cand ? best_cand : G.cbest;
+    CK(bound_launch(a, ctx->n_sm, st), "exact check");
+    ctx->launches += 5;
+    uint8_t *bm = best_m ? (dev ? best_m : (uint8_t *)b->tmp + ob_bytes) : nullptr;
+    if (bm) {
+        if (!dev && nrow) CK(cudaMemsetAsync(bm, 0, nrow, st), "clear best_m");
+        CK(gnn_pick_column(b->n_dags, b->node_off, pl.nrows, a.best_cand, G.cand, kPropStride, bm, ctx->n_sm, st),
+           "winning allocation");
+        ctx->launches++;
+    }
+    if (cand_m && nrow)
+        CK(cudaMemcpy2DAsync(cand_m, nc, G.cand, kPropStride, nc, nrow,
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st), "copy candidates");
+    if (dev) return DAGRT_OK;
+    if (out_bound && nd) CK(cudaMemcpyAsync(out_bound, a.out, 8 * nd * nc, cudaMemcpyDeviceToHost, st), "copy bounds");
+    if (best_bound && nd) CK(cudaMemcpyAsync(best_bound, a.best_bound, 8 * nd, cudaMemcpyDeviceToHost, st), "copy best");
+    if (best_cand && nd) CK(cudaMemcpyAsync(best_cand, a.best_cand, 4 * nd, cudaMemcpyDeviceToHost, st), "copy best");
+    if (best_m && nrow) CK(cudaMemcpyAsync(best_m, bm, nrow, cudaMemcpyDeviceToHost, st), "copy best_m");
+    int32_t err = 0;
+    CK(cudaMemcpyAsync(&err, b->err, sizeof err, cudaMemcpyDeviceToHost, st), "copy error word");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    if (err) return fail(ctx, err, "a wait did not complete in time");
     return DAGRT_OK;
 }

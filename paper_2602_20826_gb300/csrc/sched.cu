@@ -155,11 +155,13 @@ __device__ inline void write_failure(const SchedArgs &a, int d, int code) {
     if (a.o.n_extra) a.o.n_extra[d] = 0;
 }
 
-__device__ inline void write_row(const SchedArgs &a, const Dag &g, int r, int id, int group, uint32_t load,
-                                 uint32_t k, uint32_t m, uint64_t c) {
+// plan row r: `id` is the node (< V) or segment (>= V) it runs, `owner` the node whose
+// allocation it uses (the segment's parent for a segment)
+__device__ inline void write_row(const SchedArgs &a, const Dag &g, int r, int id, int owner, int group,
+                                 uint32_t load, uint32_t k, uint32_t m, uint64_t c) {
     if (r >= 2 * g.V) return;
     const int64_t i = g.rbase + r;
-    if (a.plan) a.plan[i] = make_uint4(load, (uint32_t)c, m | (k << 16), 0u);
+    if (a.plan) a.plan[i] = make_uint4(load, (uint32_t)c, m | (k << 16), (uint32_t)owner);
     if (a.o.row_id) a.o.row_id[i] = id;
     if (a.o.row_group) a.o.row_group[i] = group;
     if (a.o.row_m0) a.o.row_m0[i] = (int32_t)m;
@@ -167,7 +169,7 @@ __device__ inline void write_row(const SchedArgs &a, const Dag &g, int r, int id
 }
 
 // ------------------------------------------------------------------ Alg.2 pieces
-// Launch parallel nodes for group j (Alg.2 lines 7-17): released, unfinished nodes outside
+// Launch parallel nodes for group j (Alg.2's parallel-launch and segmentation step): released, unfinished nodes outside
 // pi_j in descending W^anc order (lowest rank first). One thread. Returns the number of
 // launched parts (ids in ws.lst; a segment id is >= V) and of whole-node launches.
 __device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, int j, uint64_t R, uint32_t S0,
@@ -223,7 +225,7 @@ __device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, 
                         a.o.seg_m[g.n0 + s] = (int32_t)mu;
                         a.o.seg_group[g.n0 + s] = j;
                     }
-                    write_row(a, g, acc.nrows++, g.V + s, j, (uint32_t)p, k, mu, exec_time(p, k, mu, M));
+                    write_row(a, g, acc.nrows++, g.V + s, u, j, (uint32_t)p, k, mu, exec_time(p, k, mu, M));
                     ws.rem[u] = load - (uint32_t)p;
                     ws.lst[nl++] = g.V + s;
                     stop = true;
@@ -231,7 +233,7 @@ __device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, 
                 }
                 ws.st[u] |= ST_LAUNCH;
                 ws.mm[u] = (uint16_t)mu;
-                write_row(a, g, acc.nrows++, u, j, load, k, mu, c);
+                write_row(a, g, acc.nrows++, u, u, j, load, k, mu, c);
                 ws.lst[nl++] = u;
                 nwhole++;
             }
@@ -243,7 +245,7 @@ __device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, 
     *nwhole_out = nwhole;
 }
 
-// Extra dependencies (Alg.2 line 14): (v_n, succ(v_R)) for every launched part and
+// Extra dependencies (Alg.2's segmentation step): (v_n, succ(v_R)) for every launched part and
 // (v_R, v_n) for every unlaunched parallel node, the split node's residual included. The
 // count is always kept; the edges are written when requested. One thread.
 __device__ void extra_edges(const Ws &ws, const SchedArgs &a, const Dag &g, int j, int vR, int np, int nl,
@@ -333,7 +335,7 @@ __device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int
             R = c;
             vR = v;
         }
-        write_row(a, g, acc.nrows++, v, j, x, ws.kk[v], m, c);
+        write_row(a, g, acc.nrows++, v, v, j, x, ws.kk[v], m, c);
     }
     int nl, nwhole;
     launch_parallel(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
@@ -433,7 +435,7 @@ __device__ void group_team(const Team<NT> &tm, const Ws &ws, const SchedArgs &a,
         const uint32_t off = tm.excl_sum(mem ? 1u : 0u, &tot);
         if (mem) {
             const int v = ws.gmem[i];
-            write_row(a, g, nrows + (int)off, v, j, ws.rem[v], ws.kk[v], ws.mm[v],
+            write_row(a, g, nrows + (int)off, v, v, j, ws.rem[v], ws.kk[v], ws.mm[v],
                       exec_time(ws.rem[v], ws.kk[v], ws.mm[v], M));
         }
         nrows += (int)tot;

@@ -35,7 +35,7 @@ struct SchedArgs {
     // plan of the schedule (NULL: not kept): row count, flags, rows at 2*node_off[d]
     int32_t *nrows;
     int32_t *pflag;      // per DAG: bit 0 = candidate bounds of this DAG fit 32-bit sums
-    uint4 *plan;         // rows {load, scheduled C, m | k << 16 | last-row-of-group << 24, 0}
+    uint4 *plan;         // rows {load, scheduled C, m | k << 16 | last-row-of-group << 24, owner node}
     // optional caller outputs (device pointers, NULL = skip)
     dagrt_schedule_out o;
     // global workspace of the CTA-team kernel

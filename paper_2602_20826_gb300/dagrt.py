@@ -68,6 +68,15 @@ dagrt_search = _sig("dagrt_search", C.c_int, [_vp, C.POINTER(dagrt_search_cfg), 
 dagrt_schedule_noalloc = _sig("dagrt_schedule_noalloc", C.c_int,
                               [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp])
 
+dagrt_model_n_params = _sig("dagrt_model_n_params", C.c_int64, [])
+dagrt_model_create = _sig("dagrt_model_create", C.c_int, [_vp, C.c_int32, _vp, C.c_uint64, C.POINTER(_vp)])
+dagrt_model_free = _sig("dagrt_model_free", None, [_vp])
+dagrt_model_params = _sig("dagrt_model_params", C.c_int, [_vp, _vp, _vp])
+dagrt_model_logits = _sig("dagrt_model_logits", C.c_int, [_vp, _vp, _vp, C.c_uint32])
+dagrt_model_grad = _sig("dagrt_model_grad", C.c_int, [_vp, _vp, _vp, _vp, _vp])
+dagrt_train_step = _sig("dagrt_train_step", C.c_int, [_vp, _vp, _vp, C.c_float, _vp])
+dagrt_propose = _sig("dagrt_propose", C.c_int, [_vp, _vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, C.c_uint32])
+
 
 class DagrtError(RuntimeError):
     def __init__(self, code, msg):
@@ -268,3 +277,76 @@ def schedule_noalloc(dev: dict, M: int, variant: int, bound, status, stream=None
     return int(dagrt_schedule_noalloc(n, _ptr(dev["node_off"]), _ptr(dev["edge_off"]), _ptr(dev["row_ptr"]),
                                       _ptr(dev["col"]), _ptr(dev["wcet"]), _ptr(dev["k64"]), int(M),
                                       int(variant), _ptr(bound), _ptr(status), stream))
+
+
+class Model:
+    """Learned proposer (dagrt_model_*): per-kernel SM-level scores from a message-passing
+    network; `propose` evaluates the paper's allocation and the k best assignments exactly."""
+
+    def __init__(self, ctx: Context, levels, seed: int = 0):
+        self.ctx = ctx
+        self.levels = np.ascontiguousarray(levels, np.uint8)
+        h = _vp()
+        ctx.check(dagrt_model_create(ctx.h, len(self.levels), _ptr(self.levels),
+                                     C.c_uint64(seed & (2**64 - 1)), C.byref(h)))
+        self.h = h
+        self.n_params = int(dagrt_model_n_params())
+
+    def free(self):
+        if getattr(self, "h", None):
+            dagrt_model_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def params(self, set_to=None) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        st = None if set_to is None else np.ascontiguousarray(set_to, np.float32)
+        self.ctx.check(dagrt_model_params(self.h, _ptr(out), _ptr(st)))
+        return out
+
+    def logits(self, batch: "LoadedBatch", out=None) -> np.ndarray:
+        L = len(self.levels)
+        if out is not None:  # torch CUDA tensor [total_nodes * L]
+            self.ctx.check(dagrt_model_logits(batch.h, self.h, _ptr(out), PTR_DEVICE))
+            return out
+        z = np.zeros(max(batch.total_nodes * L, 1), np.float32)
+        self.ctx.check(dagrt_model_logits(batch.h, self.h, _ptr(z), 0))
+        return z[:batch.total_nodes * L].reshape(batch.total_nodes, L)
+
+    def grad(self, batch: "LoadedBatch", labels):
+        lab = np.ascontiguousarray(labels, np.int8)
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_float(0)
+        self.ctx.check(dagrt_model_grad(batch.h, self.h, _ptr(lab), _ptr(g), C.byref(loss)))
+        return float(loss.value), g
+
+    def train_step(self, batch: "LoadedBatch", labels, lr: float) -> float:
+        lab = np.ascontiguousarray(labels, np.int8)
+        loss = C.c_float(0)
+        self.ctx.check(dagrt_train_step(batch.h, self.h, _ptr(lab), C.c_float(lr), C.byref(loss)))
+        return float(loss.value)
+
+    def propose(self, batch: "LoadedBatch", k: int = 16, want_all: bool = False, want_m: bool = False, out=None):
+        """dagrt_propose. Host outputs (numpy) by default; with `out` (dict of torch CUDA
+        tensors: out_bound/cand_m/best_bound/best_cand/best_m, any subset) the call only
+        enqueues device work."""
+        if out is not None:
+            self.ctx.check(dagrt_propose(batch.h, self.h, int(k), _ptr(out.get("out_bound")), _ptr(out.get("cand_m")),
+                                         _ptr(out.get("best_bound")), _ptr(out.get("best_cand")),
+                                         _ptr(out.get("best_m")), PTR_DEVICE))
+            return out
+        nd, nr, nc = batch.n_dags, 2 * batch.total_nodes, int(k) + 1
+        ob = np.zeros(max(nd * nc, 1), np.int64) if want_all else None
+        cm = np.zeros(max(nr * nc, 1), np.uint8) if want_all else None
+        bb = np.zeros(max(nd, 1), np.int64)
+        bc = np.zeros(max(nd, 1), np.int32)
+        bm = np.zeros(max(nr, 1), np.uint8) if want_m else None
+        self.ctx.check(dagrt_propose(batch.h, self.h, int(k), _ptr(ob), _ptr(cm), _ptr(bb), _ptr(bc), _ptr(bm), 0))
+        return {"out_bound": ob[:nd * nc].reshape(nd, nc) if want_all else None,
+                "cand_m": cm[:nr * nc].reshape(nr, nc) if want_all else None,
+                "best_bound": bb[:nd], "best_cand": bc[:nd], "best_m": bm}

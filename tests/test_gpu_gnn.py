@@ -1,0 +1,219 @@
+"""GPU parity of the learned proposer (tcgen05 forward/backward, Adam, top-k decode, exact
+check) against the float64 CPU oracle (oracle/gnn.py) and the bound oracle.
+
+Tolerances. The library stores features, aggregated layer inputs, weights and activations
+in bfloat16 and accumulates in fp32; the oracle rounds to bfloat16 at the same places and
+accumulates in float64. The two differ by fp32 accumulation error (~1e-6 relative) and,
+rarely, by one bfloat16 step (2^-8 relative) where a value lies within that error of a
+rounding boundary. The bounds below allow a few such steps per logit; the backward pass
+also rounds dZ to bfloat16 for its MMAs (2^-9 relative per element, averaging out over the
+node sums), hence the 2% relative tolerance per gradient block."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import gnn as G
+from paper_2602_20826_gb300 import workloads as wl
+from tests.gpu_helpers import context
+
+pytestmark = pytest.mark.gpu
+
+LEVELS = [1, 2, 4, 8, 16, 32]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    return context()
+
+
+def _oracle_inputs(b):
+    preds, succs = G.graph(b)
+    N = b.total_nodes()
+    level = np.zeros(N, np.int64)
+    wanc = np.zeros(N, np.int64)
+    m = np.zeros(N, np.int64)
+    plans = []
+    for d in range(b.n_dags):
+        rc, ref = oracle.schedule_dag_of(b, d, 0)
+        assert rc == 0
+        a, e = int(b.node_off[d]), int(b.node_off[d + 1])
+        level[a:e], wanc[a:e], m[a:e] = ref["level"], ref["wanc"], ref["m"]
+        plans.append(ref)
+    x = G.features(b, level, wanc, m, preds, succs)
+    return preds, succs, x, plans
+
+
+def _batch(n_dags=24, v_lo=2, v_hi=200, seed=11):
+    return wl.small_config(2, n_dags, v_lo, v_hi, seed=seed)
+
+
+@pytest.fixture(scope="module")
+def setup(ctx):
+    from paper_2602_20826_gb300.dagrt import Model
+    b = _batch()
+    lb = ctx.load(b)
+    model = Model(ctx, LEVELS, seed=7)
+    preds, succs, x, plans = _oracle_inputs(b)
+    return b, lb, model, preds, succs, x, plans
+
+
+def test_logits_match_oracle(setup):
+    b, lb, model, preds, succs, x, _ = setup
+    L = len(LEVELS)
+    z = model.logits(lb)
+    p = model.params().astype(np.float64)
+    ref, _ = G.forward(p, x, preds, succs, L, bf=True)
+    assert z.shape == ref.shape
+    scale = 1.0 + np.sqrt(np.mean(ref ** 2))
+    err = np.abs(z - ref)
+    assert err.max() <= 2e-2 * scale, err.max()
+    assert err.mean() <= 1e-3 * scale, err.mean()
+
+
+def test_logits_tile_sizes(ctx):
+    """Batches whose node counts end mid-tile and a one-node DAG."""
+    from paper_2602_20826_gb300.dagrt import Model
+    for n_dags, v_lo, v_hi, seed in ((1, 1, 1, 3), (3, 40, 90, 4), (9, 100, 260, 5)):
+        b = _batch(n_dags, v_lo, v_hi, seed)
+        lb = ctx.load(b)
+        model = Model(ctx, LEVELS[:4], seed=seed)
+        z = model.logits(lb)
+        preds, succs, x, _ = _oracle_inputs(b)
+        ref, _ = G.forward(model.params().astype(np.float64), x, preds, succs, 4, bf=True)
+        scale = 1.0 + np.sqrt(np.mean(ref ** 2))
+        assert np.abs(z - ref).max() <= 2e-2 * scale
+        model.free()
+        lb.free()
+
+
+def _blocks(v):
+    out, o = {}, 0
+    for name, shape in G._SIZES:
+        n = int(np.prod(shape))
+        out[name] = v[o:o + n]
+        o += n
+    return out
+
+
+def test_gradient_matches_oracle(setup):
+    b, lb, model, preds, succs, x, _ = setup
+    L = len(LEVELS)
+    rng = np.random.default_rng(3)
+    labels = rng.integers(-1, L, size=b.total_nodes()).astype(np.int8)
+    loss, g = model.grad(lb, labels)
+    p = model.params().astype(np.float64)
+    rl, rg = G.loss_and_grad(p, x, preds, succs, labels, L, bf=True)
+    assert abs(loss - rl) <= 1e-3 * max(1.0, rl), (loss, rl)
+    gb, rb = _blocks(g.astype(np.float64)), _blocks(rg)
+    for name in rb:
+        n = np.linalg.norm(rb[name])
+        assert np.linalg.norm(gb[name] - rb[name]) <= 2e-2 * n + 1e-7, name
+    # fixed-order reductions: a second call repeats bit for bit
+    loss2, g2 = model.grad(lb, labels)
+    assert loss2 == loss and np.array_equal(g, g2)
+
+
+def test_train_step_is_adam_on_the_gradient(ctx):
+    from paper_2602_20826_gb300.dagrt import Model
+    b = _batch(6, 20, 120, 21)
+    lb = ctx.load(b)
+    model = Model(ctx, LEVELS, seed=1)
+    # labels that the features determine (a bucket of log2 C^), so they can be fitted
+    labels = np.minimum(len(LEVELS) - 1, np.log2(b.wcet.astype(np.float64)) // 2.5).astype(np.int8)
+    p0 = model.params().astype(np.float64)
+    _, g = model.grad(lb, labels)
+    model.train_step(lb, labels, 1e-3)
+    p1 = model.params().astype(np.float64)
+    ref, _, _ = G.adam(p0, np.zeros_like(p0), np.zeros_like(p0), g.astype(np.float64), 1, 1e-3)
+    assert np.abs(p1 - ref).max() <= 1e-6
+    # training on fixed labels lowers the loss
+    losses = [model.train_step(lb, labels, 3e-3) for _ in range(40)]
+    assert losses[-1] < 0.8 * losses[0], losses[::8]
+    model.free()
+    lb.free()
+
+
+def _node_of_rows(plan):
+    V = plan["V"]
+    rid = plan["row_id"]
+    return np.where(rid < V, rid, plan["seg_parent"][np.maximum(rid - V, 0)] if plan["n_seg"] else rid)
+
+
+@pytest.mark.parametrize("k", [1, 5, 16])
+def test_propose_topk_and_exact_check(setup, k):
+    b, lb, model, preds, succs, x, plans = setup
+    L = len(LEVELS)
+    z = model.logits(lb).astype(np.float64)
+    res = model.propose(lb, k, want_all=True, want_m=True)
+    ob, cm = res["out_bound"], res["cand_m"]
+    for d in range(b.n_dags):
+        plan = plans[d]
+        a, e = int(b.node_off[d]), int(b.node_off[d + 1])
+        V, R = e - a, plan["n_rows"]
+        rows = cm[2 * a: 2 * a + R]
+        owner = _node_of_rows(plan)
+        assert np.all(rows[:, 0] == 0)
+        # each proposal: one level per node, identical on all rows of the node
+        assign = np.zeros((k, V), np.int64)
+        for j in range(k):
+            col = rows[:, 1 + j]
+            for v in range(V):
+                vals = set(col[owner == v].tolist())
+                assert len(vals) == 1, (d, j, v, vals)
+                assign[j, v] = LEVELS.index(vals.pop())
+        n_distinct = min(k, L ** V) if V < 8 else k
+        assert len({tuple(r) for r in assign}) == n_distinct
+        got = sorted(G.cost_of(z[a:e], assign[j]) for j in range(n_distinct))
+        ref = [c for c, _ in G.k_best(z[a:e], n_distinct)]
+        assert np.allclose(got, ref, atol=1e-4 * (1 + max(ref))), (d, got, ref)
+        # exact check: every candidate's bound, the argmin and its allocation
+        want = [oracle.bound_plan(plan, b.M, None if c == 0 else np.ascontiguousarray(rows[:, c]), 1)
+                for c in range(k + 1)]
+        assert np.array_equal(ob[d], want), (d, ob[d], want)
+        assert res["best_bound"][d] == min(want) and res["best_cand"][d] == int(np.argmin(want))
+        assert np.array_equal(res["best_m"][2 * a: 2 * a + R], rows[:, res["best_cand"][d]])
+        assert res["best_bound"][d] <= plan["bound"]
+
+
+def test_propose_device_outputs(ctx, setup):
+    import torch
+    b, lb, model, *_ = setup
+    host = model.propose(lb, 16, want_all=True, want_m=True)
+    nd, nr = b.n_dags, 2 * b.total_nodes()
+    out = {"out_bound": torch.zeros(nd * 17, dtype=torch.int64, device="cuda"),
+           "cand_m": torch.zeros(nr * 17, dtype=torch.uint8, device="cuda"),
+           "best_bound": torch.zeros(nd, dtype=torch.int64, device="cuda"),
+           "best_cand": torch.zeros(nd, dtype=torch.int32, device="cuda"),
+           "best_m": torch.zeros(nr, dtype=torch.uint8, device="cuda")}
+    model.propose(lb, 16, out=out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out["out_bound"].cpu().numpy().reshape(nd, 17), host["out_bound"])
+    assert np.array_equal(out["best_bound"].cpu().numpy(), host["best_bound"])
+    assert np.array_equal(out["best_cand"].cpu().numpy(), host["best_cand"])
+    assert np.array_equal(out["best_m"].cpu().numpy(), host["best_m"][:nr])
+    cm = out["cand_m"].cpu().numpy().reshape(nr, 17)
+    for d in range(nd):  # rows past each DAG's plan are unspecified
+        a = int(b.node_off[d])
+        R = setup[6][d]["n_rows"]
+        assert np.array_equal(cm[2 * a: 2 * a + R], host["cand_m"][2 * a: 2 * a + R])
+
+
+def test_model_argument_errors(ctx, setup):
+    from paper_2602_20826_gb300.dagrt import DagrtError, Model, E_INVAL
+    b, lb, model, *_ = setup
+    with pytest.raises(DagrtError) as e:
+        Model(ctx, [], seed=0)
+    assert e.value.code == E_INVAL
+    with pytest.raises(DagrtError) as e:
+        Model(ctx, [1, 0, 2], seed=0)
+    assert e.value.code == E_INVAL
+    with pytest.raises(DagrtError) as e:
+        model.propose(lb, 17)
+    assert e.value.code == E_INVAL
+    with pytest.raises(DagrtError) as e:
+        model.propose(lb, 0)
+    assert e.value.code == E_INVAL
