@@ -44,8 +44,11 @@ def _args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="dagrt", choices=["dagrt", "reference"])
-    p.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3-bound"],
-                   help="cfg2: the headline step; cfg3-bound: candidate bounds of config 3")
+    p.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3-bound", "cfg4-learned"],
+                   help="cfg2: the headline step; cfg3-bound: candidate bounds of config 3; "
+                        "cfg4-learned: learned proposal + exact check vs plain search")
+    p.add_argument("--train-dags", type=int, default=50000, help="cfg4-learned: training DAGs")
+    p.add_argument("--epochs", type=int, default=8, help="cfg4-learned: training epochs")
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="bounded CPU work of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -168,6 +171,122 @@ def run_cfg3_bound(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cfg4_learned(args):
+    """Learned proposal + exact check against the plain search, config 4.
+
+    Training (untimed): the plain search labels 50,000 DAGs of config 2's distribution;
+    the network trains on them with the library's own forward/backward kernels. Timed: on
+    10,000 fresh DAGs of 100-1,000 nodes (p = 0.05, M = 148), the plain search (4
+    structure-variant schedules + 4 x 64 generated allocations from {1,...,32}, exact bounds,
+    argmin) against dagrt_propose (paper schedule, features, network, top-16 decode, exact
+    check of the paper's allocation and the 16 proposals), each from a freshly loaded
+    device-resident batch. `value` is the learned path's time; the line also carries the
+    plain search's time and the gap between their best bounds."""
+    import torch
+    import oracle
+    from paper_2602_20826_gb300 import train as T, workloads as wl
+    from paper_2602_20826_gb300.dagrt import Context, Model
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = Context(0, stream.cuda_stream)
+    t0 = time.perf_counter()
+    data, n_nodes, chunk = [], 0, 10000
+    for c0 in range(0, args.train_dags, chunk):
+        b = wl.er_batch(min(chunk, args.train_dags - c0), 20, 200, 0.1, 148, wl.BASE_SEED + 400 + c0,
+                        name="cfg2-train")
+        labels, _ = T.search_labels(ctx, b, seed=wl.BASE_SEED + 41 + c0)
+        data.append((ctx.load(b), labels))
+        n_nodes += b.total_nodes()
+    t_lab = time.perf_counter() - t0
+    model = Model(ctx, T.LEARN_LEVELS, seed=wl.BASE_SEED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = T.train(ctx, model, data, args.epochs, 2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    for lb, _ in data:
+        lb.free()
+    del data
+    be = wl.config(4)
+    keys = ("node_off", "edge_off", "row_ptr", "col", "wcet", "k64")
+    dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(be, k))).cuda() for k in keys}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = ctx.launches()
+    reps = max(1, min(args.steps, 5))
+    outs, times = T.timed_compare(ctx, model, dev, be.M, k=16, seed=wl.BASE_SEED + 43, reps=reps)
+    launches = (ctx.launches() - l0) // (2 * (reps + 1))
+    clk = clocks.stop()
+    pb, lbest = outs["plain"]["best_bound"].astype(np.int64), outs["learned"]["best_bound"].astype(np.int64)
+    # forward-pass throughput on the eval batch (features cached by the calls above)
+    lb = ctx.load(dev, be.M)
+    zbuf = torch.empty(be.total_nodes() * len(T.LEARN_LEVELS), dtype=torch.float32, device="cuda")
+    model.logits(lb, out=zbuf)
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    fw = []
+    for _ in range(reps + 1):
+        e0, e1 = E(), E()
+        e0.record(stream)
+        model.logits(lb, out=zbuf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fw.append(e0.elapsed_time(e1))
+    t_fw = float(np.median(fw[1:])) / 1e3
+    paper = lb.schedule(0, fields=("bound",))["bound"]
+    lb.free()
+    N = be.total_nodes()
+    flops = 2.0 * N * (48 * 128 + 2 * 384 * 128 + 128 * len(T.LEARN_LEVELS))
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        tf_peak = float(json.load(f)["bf16_tflops"])
+    # end to end: host arrays in, host bests out, through the same C ABI
+    e2e = []
+    for _ in range(reps + 1):
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        lbh = ctx.load(be)
+        r = model.propose(lbh, 16)
+        lbh.free()
+        e2e.append(time.perf_counter() - ta)
+    t_e2e = float(np.median(e2e[1:]))
+    # the oracle's plain search on a sample of the eval DAGs (single thread)
+    ts = time.perf_counter()
+    ns = 0
+    while time.perf_counter() - ts < args.cpu_seconds:
+        oracle.search_dag_generated(be, ns, [0, 1, 2, 3], 64, [1, 2, 4, 8, 16, 32], wl.BASE_SEED + 43)
+        ns += 1
+    cpu_ms = (time.perf_counter() - ts) / ns * be.n_dags * 1e3
+    gap = float(lbest.sum() / pb.sum() - 1.0)
+    line = {"metric": "learned-vs-plain search time at equal bound", "value": times["learned"], "unit": "ms",
+            "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": times["learned"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/fp32 network, int64 bounds", "data": "synthetic",
+            "plain_ms": times["plain"], "speedup_vs_plain": times["plain"] / times["learned"],
+            "bound_gap_vs_plain": gap, "dags_learned_worse_than_plain": int(np.sum(lbest > pb)),
+            "dags_learned_better_than_plain": int(np.sum(lbest < pb)),
+            "dags_plain_better_than_paper": int(np.sum(pb < paper)),
+            "dags_learned_better_than_paper": int(np.sum(lbest < paper)),
+            "training": {"dags": args.train_dags, "nodes": n_nodes, "epochs": args.epochs,
+                         "label_seconds": t_lab, "train_seconds": t_train,
+                         "first_loss": losses[0], "final_loss": float(np.mean(losses[-len(losses) // args.epochs:])),
+                         "labels": "plain-search winner (4 variants x 64 allocations), nearest proposer level"},
+            "config": {"workload": "config 4: 10,000 ER DAGs 100-1,000 nodes p=0.05, M=148; learned top-16 + "
+                                   "exact check vs plain search (4 variants x 64 allocations from {1..32})",
+                       "n_dags": be.n_dags, "nodes": N, "edges": be.total_edges(),
+                       "levels": list(T.LEARN_LEVELS), "l2": "inputs 0.6 GB > L2"},
+            "e2e": {"value": 1e3 * t_e2e, "unit": "ms", "h2d_bytes_per_step": be.input_bytes(),
+                    "d2h_bytes_per_step": 12 * be.n_dags},
+            "gpu_launches": launches,
+            "roofline": {"bound": "tensor", "achieved": flops / t_fw / 1e12, "peak": tf_peak, "unit": "TFLOP/s",
+                         "frac": flops / t_fw / 1e12 / tf_peak, "traffic": None,
+                         "kernel": "network forward (3 k_gnn_fwd layers + head), dagrt_model_logits",
+                         "flops_per_launch": flops, "kernel_ms": 1e3 * t_fw,
+                         "peak_source": "measured bf16_tflops (burst)"},
+            "clocks": clk,
+            "cpu_baseline": {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": f"plain search (4 schedules + 256 bounds per DAG) on the first {ns} "
+                                       f"eval DAGs, single thread, scaled to {be.n_dags} DAGs"}}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(batch, seconds: float, gpu_bounds=None):
     """The oracle as it stands, single-threaded on this host, over whole passes of the DAGs
     in order until about `seconds` of CPU time; also checks the GPU bounds of every DAG it
@@ -233,8 +352,10 @@ def main():
         run_reference(args, rank, world)
         return
     if args.workload == "cfg3-bound":
-        import numpy as np  # noqa: F401
         run_cfg3_bound(args)
+        return
+    if args.workload == "cfg4-learned":
+        run_cfg4_learned(args)
         return
     if args.warmup < 3:
         args.warmup = 3

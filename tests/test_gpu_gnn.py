@@ -217,3 +217,35 @@ def test_model_argument_errors(ctx, setup):
     with pytest.raises(DagrtError) as e:
         model.propose(lb, 0)
     assert e.value.code == E_INVAL
+
+
+def test_gain_of_training(ctx):
+    """What training buys: the network learns the plain search's per-kernel levels (held-out
+    accuracy well above the untrained network's), and learned + exact check is never worse
+    than the paper's schedule or the plain search on fresh, larger DAGs."""
+    from paper_2602_20826_gb300 import train as T
+    from paper_2602_20826_gb300.dagrt import Model
+    tr = wl.er_batch(1500, 20, 200, 0.1, 148, 901, name="train")
+    ho = wl.er_batch(300, 20, 200, 0.1, 148, 902, name="held-out")
+    lab_tr, _ = T.search_labels(ctx, tr, seed=5)
+    lab_ho, _ = T.search_labels(ctx, ho, seed=6)
+    ltr, lho = ctx.load(tr), ctx.load(ho)
+    model = Model(ctx, T.LEARN_LEVELS, seed=3)
+
+    def acc():
+        z = model.logits(lho)
+        ok = lab_ho >= 0
+        return float(np.mean(np.argmax(z, 1)[ok] == lab_ho[ok]))
+
+    a0 = acc()
+    T.train(ctx, model, [(ltr, lab_tr)], epochs=150, lr=3e-3)
+    a1 = acc()
+    assert a1 > a0 + 0.15 and a1 > 0.5, (a0, a1)
+    ev = wl.small_config(4, 60, 100, 400, seed=903)
+    lev = ctx.load(ev)
+    paper = lev.schedule(0)["bound"]
+    for v in (1, 2, 3):
+        lev.schedule(v, fields=("status",))
+    plain = lev.search([0, 1, 2, 3], 64, [1, 2, 4, 8, 16, 32], 7)["best_bound"]
+    got = model.propose(lev, 16)["best_bound"]
+    assert np.all(got <= paper) and np.all(got <= plain)
