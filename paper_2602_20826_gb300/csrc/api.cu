@@ -81,6 +81,8 @@ struct Plan {
     int32_t *pflag = nullptr;
     int32_t *status = nullptr;
     int64_t *bound = nullptr;
+    bool chunked = false;  // ci holds this plan's chunks
+    ChunkIndex ci = {};
 };
 
 }  // namespace
@@ -107,6 +109,8 @@ struct dagrt_batch {
     // scratch for candidate evaluation
     void *tmp = nullptr;
     size_t tmp_cap = 0;
+    void *bscr = nullptr;  // work-item scratch of the bound kernels
+    size_t bscr_cap = 0;
     // learned proposer: message-passing graph, features, activations (allocated on first use)
     struct Gnn {
         bool graph = false, train = false;
@@ -163,6 +167,9 @@ static void batch_release(dagrt_batch *b) {
     if (b->tmp) b->ctx->pool.put(b->tmp, b->tmp_cap);
     b->tmp = nullptr;
     b->tmp_cap = 0;
+    if (b->bscr) b->ctx->pool.put(b->bscr, b->bscr_cap);
+    b->bscr = nullptr;
+    b->bscr_cap = 0;
 }
 
 extern "C" {
@@ -393,6 +400,41 @@ static int ensure_plan(dagrt_batch *b, int variant) {
     return DAGRT_OK;
 }
 
+// chunks of a plan for the balanced bound kernel (built once per plan)
+static int ensure_chunks(dagrt_batch *b, int variant) {
+    dagrt_ctx *ctx = b->ctx;
+    Plan &p = b->plan[variant];
+    if (p.chunked) return DAGRT_OK;
+    if (!p.ci.chunk) {
+        cudaError_t e;
+        if ((e = batch_alloc(b, &p.ci.chunk, (size_t)(2 * b->total_nodes))) != cudaSuccess ||
+            (e = batch_alloc(b, &p.ci.nchunk, (size_t)b->n_dags)) != cudaSuccess ||
+            (e = batch_alloc(b, &p.ci.cpre, (size_t)b->n_dags + 1)) != cudaSuccess ||
+            (e = batch_alloc(b, &p.ci.item, (size_t)chunk_items_bound(b->total_nodes, b->n_dags))) != cudaSuccess)
+            return cuda_fail(ctx, e, "allocate plan chunks");
+    }
+    CK(bound_build_chunks(b->n_dags, b->node_off, p.rows, p.nrows, p.status, p.ci, ctx->n_sm, ctx->stream),
+       "build plan chunks");
+    ctx->launches += 3;
+    p.chunked = true;
+    return DAGRT_OK;
+}
+
+static int ensure_bscr(dagrt_batch *b, size_t bytes) {
+    dagrt_ctx *ctx = b->ctx;
+    if (b->bscr_cap >= bytes) return DAGRT_OK;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    if (b->bscr) ctx->pool.put(b->bscr, b->bscr_cap);
+    b->bscr = nullptr;
+    b->bscr_cap = 0;
+    bytes = (bytes + 255) / 256 * 256;
+    CK(ctx->pool.get(&b->bscr, bytes), "allocate bound scratch");
+    b->bscr_cap = bytes;
+    // the work-item counter starts at zero; the bound kernels reset it after every call
+    CK(cudaMemsetAsync(b->bscr, 0, 256, ctx->stream), "clear bound scratch");
+    return DAGRT_OK;
+}
+
 static int ensure_tmp(dagrt_batch *b, size_t bytes) {
     dagrt_ctx *ctx = b->ctx;
     if (b->tmp_cap >= bytes) return DAGRT_OK;
@@ -518,6 +560,7 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
         for (int i = 0; i < nused; i++) CK(cudaStreamWaitEvent(ctx->stream, ctx->join[used[i]], 0), "join");
     }
     p.valid = true;
+    p.chunked = false;
     if (dev) return DAGRT_OK;
 
     for (auto &f : fields) {
@@ -601,8 +644,32 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
         a.best_bound = best_bound ? d_bb : nullptr;
         a.best_cand = best_cand ? d_bc : nullptr;
     }
-    CK(bound_launch(a, ctx->n_sm, ctx->stream), "launch bound kernel");
-    if (nd) ctx->launches++;
+    ChunkArgs ch;
+    std::memset(&ch, 0, sizeof ch);
+    const bool items = bound_chunk_eligible(a, b->total_nodes);
+    if (items) {
+        for (int i = 0; i < n_variants; i++) {
+            const int v = variant_ids[i];
+            int rc = ensure_chunks(b, v);
+            if (rc) return rc;
+            ch.chunk[i] = b->plan[v].ci.chunk;
+            ch.nchunk[i] = b->plan[v].ci.nchunk;
+            ch.cpre[i] = b->plan[v].ci.cpre;
+            ch.item[i] = b->plan[v].ci.item;
+        }
+        int rc = ensure_bscr(b, bound_chunk_scratch(b->n_dags, b->total_nodes, n_variants, n_alloc));
+        if (rc) return rc;
+        const size_t per_dag = (4 * nd + 255) / 256 * 256;
+        char *t = (char *)b->bscr;
+        ch.counter = (uint32_t *)t;        // the kernels' counters share the first 256 bytes
+        ch.wide_n = (int32_t *)(t + 4);
+        t += 256;
+        ch.wide_list = (int32_t *)t;
+        ch.partial = (int32_t *)(t + per_dag);
+    }
+    int nl = 0;
+    CK(bound_launch(a, items ? &ch : nullptr, ctx->n_sm, ctx->stream, &nl), "launch bound kernel");
+    ctx->launches += nl;
     if (dev) return DAGRT_OK;
     if (out_bound && out_bytes) CK(cudaMemcpyAsync(out_bound, a.out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy bounds");
     if (best_bound && nd) CK(cudaMemcpyAsync(best_bound, a.best_bound, 8 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy best");
@@ -679,8 +746,9 @@ extern "C" int dagrt_search(dagrt_batch *b, const dagrt_search_cfg *cfg, int64_t
         a.best_m = best_m ? (uint8_t *)take(m_bytes) : nullptr;
         if (best_m && m_bytes) CK(cudaMemsetAsync(a.best_m, 0, m_bytes, ctx->stream), "clear best_m");
     }
-    CK(bound_launch(a, ctx->n_sm, ctx->stream), "launch search kernel");
-    if (nd) ctx->launches++;
+    int nl = 0;
+    CK(bound_launch(a, nullptr, ctx->n_sm, ctx->stream, &nl), "launch search kernel");
+    ctx->launches += nl;
     if (dev) return DAGRT_OK;
     if (out_bound && out_bytes) CK(cudaMemcpyAsync(out_bound, a.out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy bounds");
     if (best_bound && nd) CK(cudaMemcpyAsync(best_bound, a.best_bound, 8 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy best");
@@ -1006,8 +1074,9 @@ extern "C" int dagrt_propose(dagrt_batch *b, dagrt_model *md, int32_t k, int64_t
     a.out = out_bound ? (dev ? out_bound : (int64_t *)b->tmp) : nullptr;
     a.best_bound = dev && best_bound ? best_bound : G.bbest;
     a.best_cand = dev && best_cand ? best_cand : G.cbest;
-    CK(bound_launch(a, ctx->n_sm, st), "exact check");
-    ctx->launches += 5;
+    int nl = 0;
+    CK(bound_launch(a, nullptr, ctx->n_sm, st, &nl), "exact check");
+    ctx->launches += 2 + nl;  // head, top-k, exact check (forward counted apart)
     uint8_t *bm = best_m ? (dev ? best_m : (uint8_t *)b->tmp + ob_bytes) : nullptr;
     if (bm) {
         if (!dev && nrow) CK(cudaMemsetAsync(bm, 0, nrow, st), "clear best_m");

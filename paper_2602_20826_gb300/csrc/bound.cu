@@ -10,10 +10,12 @@
 // run of T * cand_stride bytes) and the T plan rows of every variant in the call -- stream
 // from global to shared memory with TMA bulk copies into two stages that complete on
 // mbarriers, so the loads of tile i+1 overlap the evaluation of tile i. Each thread owns
-// 1, 2 or 4 adjacent candidates of one variant (one shared load per row), chosen so that a
-// warp covers a single variant when possible, keeps their running group states, and the
-// argmin over the DAG's candidates is reduced with warp shuffles and shared memory in the
-// same kernel.
+// 1, 2 or 4 adjacent candidates of one variant (one shared load per row) and keeps their
+// running group states; the argmin over the DAG's candidates is reduced with warp
+// shuffles and shared memory in the same kernel. CTAs are as small as the candidate count
+// allows (64 threads for 256 candidates), so many DAGs are in flight per SM.
+#include <type_traits>
+
 #include "bound.cuh"
 #include "dagrt_internal.cuh"
 
@@ -87,7 +89,127 @@ __host__ __device__ inline TileLayout tile_layout(int T, int64_t stride, int nv)
     return t;
 }
 
+// Candidate bytes of one row for a thread's CPT adjacent candidates (one shared load), or
+// the generated levels of those candidates.
 template <int CPT, bool GEN>
+__device__ __forceinline__ uint32_t row_alloc(const BoundArgs &a, const unsigned char *cbuf, int64_t stride, int rr,
+                                              int d, int c, int row, const uint8_t *s_lev) {
+    if (GEN) {
+        uint32_t m4 = 0;
+#pragma unroll
+        for (int q = 0; q < CPT; q++) {
+            const int cq = c + q;
+            if (cq % a.n_alloc != 0) m4 |= (uint32_t)s_lev[gen_level(a.seed, d, cq, row, a.n_levels)] << (8 * q);
+        }
+        return m4;
+    }
+    if (CPT == 4) return *(const uint32_t *)(cbuf + rr * stride);
+    if (CPT == 2) return *(const uint16_t *)(cbuf + rr * stride);
+    return cbuf[rr * stride];
+}
+
+// The tiles of DAG d for this thread's candidates c .. c+CPT-1 (variant vi, my_rows rows).
+// FIT (uniform over the DAG): every variant's plan keeps all sums below 2^31, so the
+// state is 32-bit and C for m = 2^l <= M takes the shift form
+//   ceil(x (64m - k(m-1)) / 64m) = ((x(64-k) + 64) << l + x k - 1) >> (l + 6);
+// other allocations (not a power of two, or above M) take exec_time. Group ends are
+// applied without branches, so threads of different variants may share a warp.
+// Returns false when a tile copy stalled (the CTA aborts).
+template <int CPT, bool GEN, bool FIT>
+__device__ __forceinline__ bool eval_tiles(const BoundArgs &a, int d, int c, int vi, int my_rows, int rows_max,
+                                           const TileLayout &L, int64_t stride, unsigned char *const *stage,
+                                           uint64_t *bar, uint32_t *uses, uint32_t *issued, uint32_t *landed,
+                                           int *s_abort, const uint8_t *s_lev, uint64_t *bound_out) {
+    using S = typename std::conditional<FIT, uint32_t, uint64_t>::type;
+    const int T = L.T, nv = a.n_variants, tid = threadIdx.x;
+    const uint32_t M = (uint32_t)a.M;
+    const int64_t rbase = 2 * a.node_off[d];
+    const int ntile = (rows_max + T - 1) / T;
+    S bound[CPT], gmax[CPT], gsum[CPT];
+    uint32_t gm[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; q++) bound[q] = gmax[q] = gsum[q] = 0, gm[q] = 0;
+
+    auto issue = [&](int i) {  // tile i of the DAG into stage i & 1 (thread 0)
+        const int s = i & 1;
+        const int r0 = i * T;
+        const int rn = min(T, rows_max - r0);
+        const uint32_t cb = (uint32_t)(rn * stride);
+        issued[s]++;
+        mbar_expect_tx(&bar[s], cb + (uint32_t)(nv * rn * 16));
+        if (!GEN) bulk_g2s(stage[s], a.m_alloc + (rbase + r0) * stride, cb, &bar[s]);
+        for (int v = 0; v < nv; v++)
+            bulk_g2s(stage[s] + L.cand_bytes + (int64_t)v * T * 16, a.plan[v] + rbase + r0, (uint32_t)(rn * 16),
+                     &bar[s]);
+    };
+    if (tid == 0) {
+        fence_proxy_async();
+        for (int i = 0; i < 2 && i < ntile; i++) issue(i);
+    }
+    for (int i = 0; i < ntile; i++) {
+        const int s = i & 1;
+        const bool ok = mbar_wait(&bar[s], uses[s] & 1);
+        uses[s]++;
+        landed[s] += ok;
+        if (!ok) atomicExch(s_abort, 1);
+        __syncthreads();
+        if (*s_abort) return false;
+        const int r0 = i * T;
+        const int rn = min(T, my_rows - r0);
+        const unsigned char *cbuf = stage[s] + c;  // candidate column c of row r0
+        const uint4 *pl = (const uint4 *)(stage[s] + L.cand_bytes) + (int64_t)vi * T;
+        for (int rr = 0; rr < rn; rr++) {
+            const uint4 x = pl[rr];
+            const uint32_t k = (x.z >> 16) & 0xffu, m0 = x.z & 0xffffu;
+            const bool last = (x.z >> 24) != 0;
+            const uint32_t m4 = row_alloc<CPT, GEN>(a, cbuf, stride, rr, d, c, r0 + rr, s_lev);
+            S cc[CPT];
+            if (FIT) {
+                const uint32_t A1 = x.x * (64u - k) + 64u, B1 = x.x * k - 1u;
+#pragma unroll
+                for (int q = 0; q < CPT; q++) {
+                    const uint32_t m = (m4 >> (8 * q)) & 0xffu;
+                    const uint32_t ms = m ? m : 1u;
+                    const int l = 31 - __clz(ms);
+                    uint32_t v = ((A1 << l) + B1) >> (l + 6);
+                    if ((ms != (1u << l)) | (ms > M)) v = (uint32_t)exec_time(x.x, k, ms, M);
+                    cc[q] = m ? v : x.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < CPT; q++) {
+                    const uint32_t m = (m4 >> (8 * q)) & 0xffu;
+                    cc[q] = m ? exec_time(x.x, k, m, M) : (uint64_t)x.y;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < CPT; q++) {
+                const uint32_t m = (m4 >> (8 * q)) & 0xffu;
+                gmax[q] = cc[q] > gmax[q] ? cc[q] : gmax[q];
+                gsum[q] += cc[q];
+                gm[q] += m ? m : m0;
+                const S r = gm[q] <= M ? gmax[q] : gsum[q];
+                bound[q] += last ? r : (S)0;
+                gmax[q] = last ? (S)0 : gmax[q];
+                gsum[q] = last ? (S)0 : gsum[q];
+                gm[q] = last ? 0u : gm[q];
+            }
+        }
+        __syncthreads();  // every thread is done with stage s
+        if (tid == 0 && i + 2 < ntile) {
+            fence_proxy_async();
+            issue(i + 2);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; q++) bound_out[q] = (uint64_t)bound[q];
+    return true;
+}
+
+// FIT selects the DAGs this instance evaluates (the 32-bit form exact for every variant, or
+// not); the host launches both instances over the batch, each skipping the other's DAGs,
+// so each keeps only its own state in registers.
+template <int CPT, bool GEN, bool FIT>
 __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int T) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -97,7 +219,6 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
     __shared__ uint8_t s_lev[16];
     const int nv = a.n_variants;
     const int n_cand = nv * a.n_alloc;
-    const uint32_t M = (uint32_t)a.M;
     const int64_t stride = GEN ? 0 : a.stride;  // generated candidates stream plan rows only
     const TileLayout L = tile_layout(T, stride, nv);
     if (GEN && threadIdx.x < 16) s_lev[threadIdx.x] = a.levels[threadIdx.x];
@@ -114,12 +235,18 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
     uint32_t issued[2] = {0, 0};  // copies issued per stage (thread 0)
     uint32_t landed[2] = {0, 0};  // waits that saw their copy land (thread 0)
 
-    for (int d = blockIdx.x; d < a.n_dags; d += gridDim.x) {
+    const int n_work = a.dag_list ? *a.dag_list_n : a.n_dags;
+    for (int wi = blockIdx.x; wi < n_work; wi += gridDim.x) {
+        const int d = a.dag_list ? a.dag_list[wi] : wi;
         const int64_t rbase = 2 * a.node_off[d];
         int rows_max = 0;
+        bool fit = true;  // the 32-bit form is exact for every variant
         for (int v = 0; v < nv; v++)
-            if (a.status[v][d] == DAGRT_OK) rows_max = max(rows_max, a.nrows[v][d]);
-        const int ntile = (rows_max + T - 1) / T;
+            if (a.status[v][d] == DAGRT_OK) {
+                rows_max = max(rows_max, a.nrows[v][d]);
+                fit = fit && (a.pflag[v][d] & 1);
+            }
+        if (fit != FIT) continue;  // uniform over the CTA
         int64_t best_b = 0;
         int32_t best_c = -1;
 
@@ -129,122 +256,10 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
             const int vi = active ? c / a.n_alloc : 0;
             const bool valid = active && a.status[vi][d] == DAGRT_OK;
             const int my_rows = valid ? a.nrows[vi][d] : 0;
-            const bool fit = valid && (a.pflag[vi][d] & 1);
             uint64_t bound[CPT];
-            uint64_t gmax[CPT], gsum[CPT];              // group state, 64-bit path
-            uint32_t gmax32[CPT], gsum32[CPT], gm[CPT];  // group state, 32-bit path; SM sum
-#pragma unroll
-            for (int i = 0; i < CPT; i++) bound[i] = gmax[i] = gsum[i] = gmax32[i] = gsum32[i] = gm[i] = 0;
-
-            // tile i of the DAG into stage i & 1
-            auto issue = [&](int i) {
-                const int s = i & 1;
-                const int r0 = i * T;
-                const int rn = min(T, rows_max - r0);
-                const uint32_t cb = (uint32_t)(rn * stride);
-                issued[s]++;
-                mbar_expect_tx(&bar[s], cb + (uint32_t)(nv * rn * 16));
-                if (!GEN) bulk_g2s(stage[s], a.m_alloc + (rbase + r0) * stride, cb, &bar[s]);
-                for (int v = 0; v < nv; v++)
-                    bulk_g2s(stage[s] + L.cand_bytes + (int64_t)v * T * 16, a.plan[v] + rbase + r0,
-                             (uint32_t)(rn * 16), &bar[s]);
-            };
-            if (tid == 0) {
-                fence_proxy_async();
-                for (int i = 0; i < 2 && i < ntile; i++) issue(i);
-            }
-            for (int i = 0; i < ntile; i++) {
-                const int s = i & 1;
-                const bool ok = mbar_wait(&bar[s], uses[s] & 1);
-                uses[s]++;
-                landed[s] += ok;
-                if (!ok) atomicExch(&s_abort, 1);
-                __syncthreads();
-                if (s_abort) break;
-                const int r0 = i * T;
-                const int rn = min(T, my_rows - r0);
-                const unsigned char *cbuf = stage[s] + c;  // candidate column c of row r0
-                const uint4 *pl = (const uint4 *)(stage[s] + L.cand_bytes) + (int64_t)vi * T;
-                for (int rr = 0; rr < rn; rr++) {
-                    const uint4 x = pl[rr];
-                    const uint32_t k = (x.z >> 16) & 0xffu, m0 = x.z & 0xffffu;
-                    const bool last = (x.z >> 24) != 0;
-                    uint32_t m4;
-                    if (GEN) {
-                        m4 = 0;
-#pragma unroll
-                        for (int q = 0; q < CPT; q++) {
-                            const int cq = c + q;
-                            if (cq % a.n_alloc != 0)
-                                m4 |= (uint32_t)s_lev[gen_level(a.seed, d, cq, r0 + rr, a.n_levels)] << (8 * q);
-                        }
-                    } else if (CPT == 4) {
-                        m4 = *(const uint32_t *)(cbuf + rr * stride);
-                    } else if (CPT == 2) {
-                        m4 = *(const uint16_t *)(cbuf + rr * stride);
-                    } else {
-                        m4 = cbuf[rr * stride];
-                    }
-                    if (fit) {
-                        // C for m = 2^l <= M, 32-bit exact for this DAG:
-                        // ceil(x (64m - k(m-1)) / 64m) = ((x(64-k) + 64) << l + x k - 1) >> (l + 6)
-                        const uint32_t A1 = x.x * (64u - k) + 64u, B1 = x.x * k - 1u;
-                        uint32_t cc[CPT];
-                        bool slow = false;
-#pragma unroll
-                        for (int q = 0; q < CPT; q++) {
-                            const uint32_t m = (m4 >> (8 * q)) & 0xffu;
-                            const int l = 31 - __clz(m | (m == 0));
-                            cc[q] = m ? ((A1 << l) + B1) >> (l + 6) : x.y;
-                            slow |= ((m & (m - 1)) != 0) | (m > M);
-                        }
-                        if (slow) {  // an allocation that is not a power of two, or above M
-#pragma unroll
-                            for (int q = 0; q < CPT; q++) {
-                                const uint32_t m = (m4 >> (8 * q)) & 0xffu;
-                                if (((m & (m - 1)) != 0) | (m > M)) cc[q] = (uint32_t)exec_time(x.x, k, m, M);
-                            }
-                        }
-#pragma unroll
-                        for (int q = 0; q < CPT; q++) {
-                            const uint32_t m = (m4 >> (8 * q)) & 0xffu;
-                            gmax32[q] = cc[q] > gmax32[q] ? cc[q] : gmax32[q];
-                            gsum32[q] += cc[q];
-                            gm[q] += m ? m : m0;
-                        }
-                        if (last) {
-#pragma unroll
-                            for (int q = 0; q < CPT; q++) {
-                                bound[q] += gm[q] <= M ? gmax32[q] : gsum32[q];
-                                gmax32[q] = gsum32[q] = gm[q] = 0;
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < CPT; q++) {
-                            const uint32_t m = (m4 >> (8 * q)) & 0xffu;
-                            const uint64_t ccw = m ? exec_time(x.x, k, m, M) : (uint64_t)x.y;
-                            gmax[q] = ccw > gmax[q] ? ccw : gmax[q];
-                            gsum[q] += ccw;
-                            gm[q] += m ? m : m0;
-                        }
-                        if (last) {
-#pragma unroll
-                            for (int q = 0; q < CPT; q++) {
-                                bound[q] += gm[q] <= M ? gmax[q] : gsum[q];
-                                gmax[q] = gsum[q] = 0;
-                                gm[q] = 0;
-                            }
-                        }
-                    }
-                }
-                __syncthreads();  // every thread is done with stage s
-                if (tid == 0 && i + 2 < ntile) {
-                    fence_proxy_async();
-                    issue(i + 2);
-                }
-            }
-            if (s_abort) break;
+            const bool ok = eval_tiles<CPT, GEN, FIT>(a, d, c, vi, my_rows, rows_max, L, stride, stage, bar, uses,
+                                                      issued, landed, &s_abort, s_lev, bound);
+            if (!ok) break;
 #pragma unroll
             for (int q = 0; q < CPT; q++) {
                 const int cq = c + q;
@@ -291,15 +306,352 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
     }
 }
 
-cudaError_t bound_launch(const BoundArgs &a, int n_sm, cudaStream_t st) {
+// ------------------------------------------------------------------ balanced work items
+constexpr int kSubRows = 32;     // plan rows staged per load phase of a work item
+constexpr int kChunkWarps = 4;   // warps per CTA of the work-item kernel
+// per warp: two staging buffers (candidate bytes + plan rows) and one {C, m} table
+constexpr int kStageBytes = kSubRows * 64 + kSubRows * 16;
+constexpr int kWarpBytes = 2 * kStageBytes + kSubRows * 9 * 8;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Chunk starts of every DAG of one plan (one warp per DAG). Chunk 0 starts at row 0; a new
+// chunk starts at the first row p >= start + kChunkRows whose previous row ends a group.
+// The group-end bits of 32 rows at a time come from one ballot; every lane walks the same
+// mask, lane 0 writes.
+__global__ void k_plan_chunks(int32_t n_dags, const int64_t *node_off, const uint4 *plan, const int32_t *nrows,
+                              const int32_t *status, int32_t *chunk, int32_t *nchunk) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dags; d += warps) {
+        const int rows = status[d] == DAGRT_OK ? nrows[d] : 0;
+        const int64_t rbase = 2 * node_off[d];
+        int count = 0, cur = 0;
+        if (rows > 0) {
+            if (lane == 0) chunk[rbase] = 0;
+            count = 1;
+        }
+        for (int base = 0; base < rows; base += 32) {
+            const int r = base + lane;
+            const bool endg = r < rows && (plan[rbase + r].z >> 24) != 0;
+            const uint32_t mask = __ballot_sync(FULL, endg);
+            for (;;) {
+                const int lo = cur + kChunkRows - 1 - base;  // bit i gives the start p = base + i + 1
+                if (lo > 31) break;
+                const uint32_t mm = lo <= 0 ? mask : (mask & (~0u << lo));
+                if (!mm) break;
+                const int p = base + __ffs(mm);
+                if (p >= rows) break;
+                if (lane == 0) chunk[rbase + count] = p;
+                count++;
+                cur = p;
+            }
+        }
+        if (lane == 0) nchunk[d] = count;
+    }
+}
+
+// exclusive prefix sum of n counts (one CTA of 1024 threads); out[n] = total
+__global__ void __launch_bounds__(1024) k_scan_excl(int32_t n, const int32_t *in, int32_t *out) {
+    __shared__ int32_t ws[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int32_t carry = 0;
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + tid;
+        const int32_t x = i < n ? in[i] : 0;
+        int32_t incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) ws[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            int32_t v = ws[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(FULL, v, o);
+                if (lane >= o) v += y;
+            }
+            ws[lane] = v;
+        }
+        __syncthreads();
+        if (i < n) out[i] = carry + (w ? ws[w - 1] : 0) + incl - x;
+        const int32_t tot = ws[31];
+        __syncthreads();
+        carry += tot;
+    }
+    if (tid == 0) out[n] = carry;
+}
+
+// item records {d, first row, end row} in global plan-row numbering
+__global__ void k_fill_items(int32_t n_dags, const int64_t *node_off, const int32_t *nrows, const int32_t *chunk,
+                             const int32_t *nchunk, const int32_t *cpre, int4 *item) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dags; d += warps) {
+        const int64_t rbase = 2 * node_off[d];
+        const int nch = nchunk[d];
+        for (int k = lane; k < nch; k += 32) {
+            const int r0 = chunk[rbase + k], r1 = k + 1 < nch ? chunk[rbase + k + 1] : nrows[d];
+            item[cpre[d] + k] = make_int4(d, (int)(rbase + r0), (int)(rbase + r1), 0);
+        }
+    }
+}
+
+cudaError_t bound_build_chunks(int32_t n_dags, const int64_t *node_off, const uint4 *plan, const int32_t *nrows,
+                               const int32_t *status, const ChunkIndex &ci, int n_sm, cudaStream_t st) {
+    if (n_dags == 0) return cudaMemsetAsync(ci.cpre, 0, sizeof(int32_t), st);
+    int grid = (n_dags + 7) / 8;
+    if (grid > 16 * n_sm) grid = 16 * n_sm;
+    k_plan_chunks<<<grid, 256, 0, st>>>(n_dags, node_off, plan, nrows, status, ci.chunk, ci.nchunk);
+    k_scan_excl<<<1, 1024, 0, st>>>(n_dags, ci.nchunk, ci.cpre);
+    k_fill_items<<<grid, 256, 0, st>>>(n_dags, node_off, nrows, ci.chunk, ci.nchunk, ci.cpre, ci.item);
+    return cudaGetLastError();
+}
+
+static int64_t chunk_items_call(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc) {
+    return (int64_t)n_variants * chunk_items_bound(total_nodes, n_dags) * (n_alloc / 64);
+}
+
+bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes) {
+    return !a.gen && a.n_alloc % 64 == 0 && a.n_dags > 0 && !a.dag_list &&
+           chunk_items_call(a.n_dags, total_nodes, a.n_variants, a.n_alloc) < (1ll << 30) &&
+           2 * total_nodes < (1ll << 31);
+}
+
+size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc) {
+    return 256 + ((size_t)(4 * n_dags + 255) / 256 * 256) +
+           (size_t)chunk_items_call(n_dags, total_nodes, n_variants, n_alloc) * 64 * 4;
+}
+
+// After the work items (one CTA per DAG): a DAG whose sums fit 32 bits gets its candidate
+// bounds from its items' partial sums (one thread per candidate) and the argmin; any other
+// DAG goes to the list of the 64-bit kernel. Block 0 also resets the work-item counter
+// for the next call.
+__global__ void __launch_bounds__(256) k_bound_finish(BoundArgs a, ChunkArgs ch) {
+    __shared__ int64_t s_cum[kMaxVariantsPerCall + 1];
+    __shared__ int s_fit;
+    __shared__ int64_t s_bb[8];
+    __shared__ int32_t s_bc[8];
+    const int nv = a.n_variants, ncb = a.n_alloc / 64, n_cand = nv * a.n_alloc;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) {
+        s_cum[0] = 0;
+        for (int v = 0; v < nv; v++) s_cum[v + 1] = s_cum[v] + (int64_t)ch.cpre[v][a.n_dags] * ncb;
+        if (blockIdx.x == 0) *ch.counter = 0u;
+    }
+    for (int d = blockIdx.x; d < a.n_dags; d += gridDim.x) {
+        if (tid == 0) {
+            bool fit = true;
+            for (int v = 0; v < nv; v++)
+                if (a.status[v][d] == DAGRT_OK) fit = fit && (a.pflag[v][d] & 1);
+            s_fit = fit;
+            if (!fit) ch.wide_list[atomicAdd(ch.wide_n, 1)] = d;
+        }
+        __syncthreads();
+        if (!s_fit) {
+            __syncthreads();
+            continue;
+        }
+        int64_t best_b = 0;
+        int32_t best_c = -1;
+        for (int c = tid; c < n_cand; c += blockDim.x) {
+            const int vi = c / a.n_alloc, cc = c - vi * a.n_alloc;
+            int64_t b = -1;
+            if (a.status[vi][d] == DAGRT_OK) {
+                const int nch = ch.nchunk[vi][d];
+                const int32_t *pp = ch.partial + (s_cum[vi] + (int64_t)ch.cpre[vi][d] * ncb + (cc >> 6)) * 64 + (cc & 63);
+                b = 0;
+                for (int k = 0; k < nch; k++) b += pp[(int64_t)k * ncb * 64];
+                better(best_b, best_c, b, c);
+            }
+            if (a.out) a.out[(int64_t)d * n_cand + c] = b;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t ob = __shfl_xor_sync(FULL, best_b, o);
+            const int32_t oc = __shfl_xor_sync(FULL, best_c, o);
+            better(best_b, best_c, ob, oc);
+        }
+        if (lane == 0) {
+            s_bb[w] = best_b;
+            s_bc[w] = best_c;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int i = 1; i < (int)(blockDim.x >> 5); i++) better(best_b, best_c, s_bb[i], s_bc[i]);
+            if (a.best_bound) a.best_bound[d] = best_c < 0 ? -1 : best_b;
+            if (a.best_cand) a.best_cand[d] = best_c;
+        }
+        __syncthreads();
+    }
+}
+
+// Persistent warps over the work items. Per item: its rows (64 candidate bytes and the plan
+// row each, at most kSubRows per phase) are staged by cp.async -- the next item's first
+// phase is staged while this one computes -- then each lane builds the {C, m} table of one
+// row: m = 0 (the schedule's own C and m) and m = 1, 2, 4, ..., 128 (the 32-bit shift form;
+// exec_time above M when CHECK_M). Each lane then runs 2 candidates along the rows with
+// table lookups, taking exec_time only for bytes that are not 0 or a power of two; a group
+// of one row adds its C directly. Each item writes 64 partial sums; k_bound_finish adds
+// them up per candidate once every item is done.
+template <bool CHECK_M>
+__global__ void __launch_bounds__(kChunkWarps * 32) k_bound_items(BoundArgs a, ChunkArgs ch) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ int64_t s_cum[kMaxVariantsPerCall + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned char *wbase = sm + w * kWarpBytes;
+    uint2 *tbuf = (uint2 *)(wbase + 2 * kStageBytes);
+    const int nv = a.n_variants, ncb = a.n_alloc / 64;
+    const uint32_t M = (uint32_t)a.M;
+    if (threadIdx.x == 0) {
+        s_cum[0] = 0;
+        for (int v = 0; v < nv; v++) s_cum[v + 1] = s_cum[v] + (int64_t)ch.cpre[v][a.n_dags] * ncb;
+        if (blockIdx.x == 0) *ch.wide_n = 0;  // filled by k_bound_finish, which runs after this kernel
+    }
+    __syncthreads();
+    const uint32_t total = (uint32_t)s_cum[nv];
+
+    auto grab = [&]() -> uint32_t {
+        uint32_t v = 0;
+        if (lane == 0) v = atomicAdd(ch.counter, 1u);
+        return __shfl_sync(FULL, v, 0);
+    };
+    // variant slot, 64-candidate block and record of item j
+    auto locate = [&](uint32_t j, int &vi, int &cb, int4 &rec) {
+        vi = 0;
+        while ((int64_t)j >= s_cum[vi + 1]) vi++;
+        const uint32_t jj = j - (uint32_t)s_cum[vi];
+        const uint32_t q = jj / (uint32_t)ncb;
+        cb = (int)(jj - q * (uint32_t)ncb);
+        rec = ch.item[vi][q];
+    };
+    // rows [g0, g1) of item (vi, cb) into staging buffer b
+    auto stage = [&](int b, int vi, int cb, int g0, int g1) {
+        unsigned char *cbuf = wbase + b * kStageBytes;
+        uint4 *pbuf = (uint4 *)(cbuf + kSubRows * 64);
+        const unsigned char *src = a.m_alloc + (int64_t)vi * a.n_alloc + cb * 64;
+        const int rn = g1 - g0;
+        for (int g = lane; g < rn * 4; g += 32)
+            cp_async16(cbuf + g * 16, src + (int64_t)(g0 + (g >> 2)) * a.stride + (g & 3) * 16);
+        if (lane < rn) cp_async16(pbuf + lane, a.plan[vi] + g0 + lane);
+    };
+
+    uint32_t j = grab();
+    int vi = 0, cb = 0, buf = 0;
+    int4 rec = make_int4(0, 0, 0, 0);
+    if (j < total) {
+        locate(j, vi, cb, rec);
+        stage(0, vi, cb, rec.y, min(rec.z, rec.y + kSubRows));
+    }
+    while (j < total) {
+        const uint32_t jn = grab();
+        int vn = 0, cbn = 0;
+        int4 recn = make_int4(0, 0, 0, 0);
+        if (jn < total) locate(jn, vn, cbn, recn);
+        uint32_t gmax0 = 0, gmax1 = 0, gsum0 = 0, gsum1 = 0, gm0 = 0, gm1 = 0, b0 = 0, b1 = 0;
+        bool first = true;  // chunks start at a group start
+        bool prefetched = false;
+        for (int g0 = rec.y; g0 < rec.z; g0 += kSubRows) {
+            const int rn = min(kSubRows, rec.z - g0);
+            cp_async_wait_all();
+            __syncwarp();
+            const bool more = g0 + kSubRows < rec.z;
+            if (!more && jn < total) {  // stage the next item while this phase computes
+                stage(buf ^ 1, vn, cbn, recn.y, min(recn.z, recn.y + kSubRows));
+                prefetched = true;
+            }
+            const unsigned char *cbuf = wbase + buf * kStageBytes;
+            const uint4 *pbuf = (const uint4 *)(cbuf + kSubRows * 64);
+            if (lane < rn) {  // {C, m} table of row `lane`
+                const uint4 x = pbuf[lane];
+                const uint32_t kk = (x.z >> 16) & 0xffu;
+                const uint32_t A1 = x.x * (64u - kk) + 64u, B1 = x.x * kk - 1u;
+                uint2 *t = tbuf + lane * 9;
+                t[0] = make_uint2(x.y, x.z & 0xffffu);
+#pragma unroll
+                for (int l = 0; l < 8; l++) {
+                    uint32_t v = ((A1 << l) + B1) >> (l + 6);
+                    if (CHECK_M && (1u << l) > M) v = (uint32_t)exec_time(x.x, kk, 1u << l, M);
+                    t[l + 1] = make_uint2(v, 1u << l);
+                }
+            }
+            __syncwarp();
+#pragma unroll 2
+            for (int r = 0; r < rn; r++) {
+                const uint32_t w2 = *(const uint16_t *)(cbuf + r * 64 + 2 * lane);
+                const uint32_t z = pbuf[r].z;
+                const bool last = (z >> 24) != 0;
+                const uint32_t ma = w2 & 0xffu, mb = w2 >> 8;
+                uint2 ta = tbuf[r * 9 + 32 - __clz(ma)], tb = tbuf[r * 9 + 32 - __clz(mb)];
+                if (((w2 | 0x8080u) - 0x0101u) & w2) {  // a byte that is neither 0 nor a power of two
+                    const uint4 x = pbuf[r];
+                    const uint32_t kk = (x.z >> 16) & 0xffu;
+                    if (ma & (ma - 1)) ta = make_uint2((uint32_t)exec_time(x.x, kk, ma, M), ma);
+                    if (mb & (mb - 1)) tb = make_uint2((uint32_t)exec_time(x.x, kk, mb, M), mb);
+                }
+                if (first && last) {  // a group of one row: R = C (Lemma 1 either way)
+                    b0 += ta.x;
+                    b1 += tb.x;
+                } else {
+                    gmax0 = max(gmax0, ta.x);
+                    gmax1 = max(gmax1, tb.x);
+                    gsum0 += ta.x;
+                    gsum1 += tb.x;
+                    gm0 += ta.y;
+                    gm1 += tb.y;
+                    if (last) {
+                        b0 += gm0 <= M ? gmax0 : gsum0;
+                        b1 += gm1 <= M ? gmax1 : gsum1;
+                        gmax0 = gmax1 = gsum0 = gsum1 = gm0 = gm1 = 0;
+                    }
+                }
+                first = last;
+            }
+            __syncwarp();
+            if (more) stage(buf, vi, cb, g0 + kSubRows, min(rec.z, g0 + 2 * kSubRows));
+        }
+        if (!prefetched && jn < total) stage(buf ^ 1, vn, cbn, recn.y, min(recn.z, recn.y + kSubRows));
+        // item j's partial sums (garbage for a DAG that needs 64-bit sums: never read)
+        *(uint2 *)(ch.partial + (int64_t)j * 64 + 2 * lane) = make_uint2(b0, b1);
+        j = jn;
+        vi = vn;
+        cb = cbn;
+        rec = recn;
+        buf ^= 1;
+    }
+    cp_async_wait_all();
+}
+
+cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cudaStream_t st, int *launches) {
+    *launches = 0;
     if (a.n_dags == 0) return cudaSuccess;
     const int n_cand = a.n_variants * a.n_alloc;
-    // candidates per thread: a warp should cover candidates of one variant only (uniform
-    // group boundaries), and a thread's candidates must never straddle two variants
-    int cpt = 1;
-    for (int q : {4, 2})
-        if (a.n_alloc % (32 * q) == 0) { cpt = q; break; }
-    if (cpt == 1 && a.n_alloc % 32 != 0) cpt = a.n_alloc % 4 == 0 ? 4 : (a.n_alloc % 2 == 0 ? 2 : 1);
+    const bool items = ch != nullptr;
+    BoundArgs aw = a;  // the 64-bit kernel: all DAGs, or the list the work items leave
+    if (items) {
+        // the item counter is zero here: set when the scratch was allocated, and reset by
+        // k_bound_finish at the end of every call
+        cudaError_t e;
+        const int smem = kChunkWarps * kWarpBytes;
+        auto kern = a.M < 128 ? k_bound_items<true> : k_bound_items<false>;
+        int per_sm = 0;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChunkWarps * 32, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        kern<<<per_sm * n_sm, kChunkWarps * 32, smem, st>>>(a, *ch);
+        const int g = a.n_dags < 16 * n_sm ? a.n_dags : 16 * n_sm;
+        k_bound_finish<<<g, 256, 0, st>>>(a, *ch);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 2;
+        aw.dag_list = ch->wide_list;
+        aw.dag_list_n = ch->wide_n;
+    }
+    // candidates per thread: a thread's candidates must never straddle two variants
+    const int cpt = a.n_alloc % 4 == 0 ? 4 : (a.n_alloc % 2 == 0 ? 2 : 1);
     int threads = (n_cand + cpt - 1) / cpt;
     threads = (threads + 31) / 32 * 32;
     if (threads > kBoundMaxThreads) threads = kBoundMaxThreads;
@@ -310,18 +662,30 @@ cudaError_t bound_launch(const BoundArgs &a, int n_sm, cudaStream_t st) {
     const TileLayout L = tile_layout(T, a.gen ? 0 : a.stride, a.n_variants);
     const int64_t smem = 2 * L.stage_bytes;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    void (*kern)(BoundArgs, int) =
-        a.gen ? (cpt == 4 ? k_bound_tma<4, true> : cpt == 2 ? k_bound_tma<2, true> : k_bound_tma<1, true>)
-              : (cpt == 4 ? k_bound_tma<4, false> : cpt == 2 ? k_bound_tma<2, false> : k_bound_tma<1, false>);
-    int per_sm = 0;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    int grid = a.n_dags;
-    if (grid > per_sm * n_sm) grid = per_sm * n_sm;
-    kern<<<grid, threads, smem, st>>>(a, T);
-    return cudaGetLastError();
+    using K = void (*)(BoundArgs, int);
+    const K fast = a.gen ? (cpt == 4 ? k_bound_tma<4, true, true> : cpt == 2 ? k_bound_tma<2, true, true>
+                                                                           : k_bound_tma<1, true, true>)
+                         : (cpt == 4 ? k_bound_tma<4, false, true> : cpt == 2 ? k_bound_tma<2, false, true>
+                                                                             : k_bound_tma<1, false, true>);
+    const K wide = a.gen ? (cpt == 4 ? k_bound_tma<4, true, false> : cpt == 2 ? k_bound_tma<2, true, false>
+                                                                            : k_bound_tma<1, true, false>)
+                         : (cpt == 4 ? k_bound_tma<4, false, false> : cpt == 2 ? k_bound_tma<2, false, false>
+                                                                              : k_bound_tma<1, false, false>);
+    for (K kern : {fast, wide}) {
+        if (items && kern == fast) continue;  // the work items took these DAGs
+        int per_sm = 0;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        int grid = a.n_dags;
+        if (grid > per_sm * n_sm) grid = per_sm * n_sm;
+        if (kern == wide && grid > 2 * n_sm) grid = 2 * n_sm;  // few DAGs need the 64-bit form
+        kern<<<grid, threads, smem, st>>>(kern == wide ? aw : a, T);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*launches;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace dagrt

@@ -35,6 +35,9 @@ struct BoundArgs {
     int32_t n_levels;
     uint8_t levels[16];
     uint8_t *best_m;                            // [2*total_nodes] winning allocation or NULL
+    // optional DAG list: the kernels evaluate dag_list[0 .. *dag_list_n) only
+    const int32_t *dag_list;
+    const int32_t *dag_list_n;
 };
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014) on a counter
@@ -51,6 +54,46 @@ __host__ __device__ inline int gen_level(uint64_t seed, int64_t d, int64_t c, in
     return (int)(((splitmix64(x) >> 32) * (uint64_t)n_levels) >> 32);
 }
 
-cudaError_t bound_launch(const BoundArgs &a, int n_sm, cudaStream_t st);
+// ---------------------------------------------------------------- balanced work items
+// For materialised candidates (n_alloc a multiple of 64) whose DAG keeps every sum below
+// 2^31, the bound is evaluated per work item = (variant, DAG, chunk of ~kChunkRows plan rows
+// cut at a group end, block of 64 candidates): the bound is a sum over groups (Theorem 1),
+// so chunks evaluate independently and their partial sums add up. Chunks are a property of
+// the plan and are built once per plan.
+constexpr int kChunkRows = 24;
+
+// upper bound on the chunks of one plan (every chunk but a DAG's last has >= kChunkRows rows)
+inline int64_t chunk_items_bound(int64_t total_nodes, int32_t n_dags) {
+    return 2 * total_nodes / kChunkRows + n_dags + 1;
+}
+
+struct ChunkIndex {  // device arrays of one plan
+    int32_t *chunk;   // [2*total_nodes]: chunk k of DAG d starts at row chunk[2*node_off[d] + k]
+    int32_t *nchunk;  // [n_dags]: 0 where the DAG's schedule failed
+    int32_t *cpre;    // [n_dags + 1]: exclusive prefix sum of nchunk
+    int4 *item;       // [cpre[n_dags]]: {d, first global plan row, end global plan row, 0}, DAG-major
+};
+
+cudaError_t bound_build_chunks(int32_t n_dags, const int64_t *node_off, const uint4 *plan, const int32_t *nrows,
+                               const int32_t *status, const ChunkIndex &ci, int n_sm, cudaStream_t st);
+
+struct ChunkArgs {
+    const int32_t *chunk[kMaxVariantsPerCall], *nchunk[kMaxVariantsPerCall], *cpre[kMaxVariantsPerCall];
+    const int4 *item[kMaxVariantsPerCall];
+    uint32_t *counter;            // work-item counter
+    int32_t *wide_n;              // DAGs left to the 64-bit kernel ...
+    int32_t *wide_list;           // ... and their ids [n_dags]
+    int32_t *partial;             // [items * 64] partial bounds
+};
+
+// scratch bytes the balanced path needs for a call (counters, wide list, partials)
+size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc);
+// the call can take the balanced path (materialised candidates, n_alloc % 64 == 0, and few
+// enough work items for 32-bit item ids)
+bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes);
+
+// Enqueue the bound kernels; *launches receives the number of kernels enqueued. With ch
+// (and an eligible call), the balanced path takes the DAGs whose sums fit 32 bits.
+cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cudaStream_t st, int *launches);
 
 }  // namespace dagrt

@@ -87,3 +87,38 @@ def test_unscheduled_variant_is_rejected(ctx):
     lb = ctx.load(b)
     with pytest.raises(DagrtError):
         lb.bound([1], 4, alloc, stride)
+
+
+def test_work_item_path_arbitrary_bytes(ctx):
+    """n_alloc a multiple of 64 takes the balanced work-item kernel (chunks of plan rows cut
+    at group ends): any byte value, M below and above 128 (table entries above M), DAGs
+    whose sums need 64 bits mixed in (those go to the 64-bit kernel), one-node DAGs, and
+    repeated calls on the same scratch."""
+    rng = np.random.default_rng(23)
+    for M, n_alloc in ((1, 64), (8, 128), (100, 64), (148, 64), (4096, 64)):
+        dags = [random_small_dag(rng, int(rng.integers(1, 90)), 0.1, int(rng.choice([10, 10**4, 10**4, 2**32 - 1])))
+                for _ in range(40)]
+        b = wl.from_dags(dags, M)
+        alloc, stride = wl.candidate_allocations(b, 2, n_alloc, list(range(0, 256)), seed=M, keep_scheduled=True)
+        _run(ctx, b, [0, 3], n_alloc, alloc, stride)
+        pow2, stride2 = wl.candidate_allocations(b, 2, n_alloc, [1, 2, 4, 8, 16, 32, 64, 128], seed=M + 1)
+        _run(ctx, b, [3, 0], n_alloc, pow2, stride2)
+
+
+def test_work_item_path_long_dags_and_reschedule(ctx):
+    """DAGs of several hundred plan rows (many chunks, chunks longer than one staging
+    phase) and a plan recomputed between two calls (its chunks are rebuilt)."""
+    b = wl.config(3, n_dags=24)
+    alloc, stride = wl.candidate_allocations(b, 4, 64, [1, 2, 4, 8, 16, 32, 3, 5], seed=99)
+    lb = ctx.load(b)
+    for v in range(4):
+        lb.schedule(v, fields=("status",))
+    ob1, bb1, bc1 = lb.bound([0, 1, 2, 3], 64, alloc, stride)
+    lb.schedule(1, fields=("status",))
+    ob2, bb2, bc2 = lb.bound([0, 1, 2, 3], 64, alloc, stride)
+    assert np.array_equal(ob1, ob2) and np.array_equal(bb1, bb2) and np.array_equal(bc1, bc2)
+    for d in range(0, 24, 3):
+        ref, rb, rc = oracle.search_dag(b, d, alloc, stride, 4, 64, [0, 1, 2, 3])
+        assert np.array_equal(ob1[d], ref), (d, np.nonzero(ob1[d] != ref)[0][:5])
+        assert bb1[d] == rb and bc1[d] == rc
+    lb.free()
