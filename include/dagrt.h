@@ -80,8 +80,9 @@ int dagrt_set_stream(dagrt_ctx *ctx, void *cuda_stream);
 /* Synchronise the context's stream and report any CUDA error seen on it. */
 int dagrt_sync(dagrt_ctx *ctx);
 
-/* Free a context and every device buffer it owns. Batches created from it must be freed
- * first. NULL is ignored. */
+/* Free a context and every device buffer it owns. If batches, models or graphs of the
+ * context are still alive, the context is freed when the last of them is (so they stay
+ * usable until then). NULL is ignored. */
 void dagrt_destroy(dagrt_ctx *ctx);
 
 /* Text of the last error on this context ("" if none). Valid until the next call. */
@@ -232,6 +233,57 @@ int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_
                            const int32_t *row_ptr, const int32_t *col, const int64_t *wcet,
                            const uint8_t *k64, int32_t M, int32_t variant, int64_t *bound,
                            int32_t *status, void *cuda_stream);
+
+/* ---------------------------------------------------------------- batching controls
+ * Launch-shape choices of the batched kernels. None of them changes a result: every
+ * setting gives bit-identical outputs; they only move work between kernels.
+ *   warp_max_v  scheduler: DAGs of at most this many nodes (and at most 12 edges per node
+ *               of their class) are scheduled by warp teams in shared memory, larger ones by
+ *               CTA teams with global workspaces; one of 0 (CTA teams only), 64, 128, 192,
+ *               256. Default 256.
+ *   chunk_rows  candidate bounds: the plan rows of a DAG are cut into work items of about
+ *               this many rows at group ends (Theorem 1's sum splits there); 8 .. 256.
+ *               Default 24.
+ *   item_warps  candidate bounds: warps per CTA of the work-item kernel, 1 .. 8. Default 4. */
+typedef struct {
+    int32_t warp_max_v;
+    int32_t chunk_rows;
+    int32_t item_warps;
+} dagrt_tuning;
+
+int dagrt_get_tuning(const dagrt_batch *batch, dagrt_tuning *out);
+/* Validates and applies t (DAGRT_E_INVAL on a value outside the ranges above). Host work
+ * and one upload; synchronises the context's stream. */
+int dagrt_set_tuning(dagrt_batch *batch, const dagrt_tuning *t);
+
+/* Autotuner. Times dagrt_schedule(batch, variant) (device outputs) for every warp_max_v
+ * in {64, 128, 192, 256}, `reps` times each after one warm-up (CUDA events on the
+ * context's stream), keeps the fastest setting in the batch and returns it (*best_ms: its
+ * median time). Synchronous. */
+int dagrt_autotune_schedule(dagrt_batch *batch, int32_t variant, int32_t reps, dagrt_tuning *chosen,
+                            float *best_ms);
+/* Same for dagrt_bound with the given candidates (device m_alloc; every variant must have
+ * been scheduled): chunk_rows in {16, 24, 32, 48} x item_warps in {2, 4, 8}. Only calls
+ * that take the work-item kernel (n_alloc a multiple of 64) have anything to tune;
+ * others return the current setting unchanged. */
+int dagrt_autotune_bound(dagrt_batch *batch, int32_t n_variants, const int32_t *variant_ids,
+                         int32_t n_alloc, const uint8_t *m_alloc, int64_t cand_stride, int32_t reps,
+                         dagrt_tuning *chosen, float *best_ms);
+
+/* ---------------------------------------------------------------- CUDA graphs
+ * dagrt_graph_begin synchronises the context's stream and starts capturing (relaxed capture mode, on
+ * a private stream of the context, so that the legacy default stream works too); every
+ * library call made with DAGRT_PTR_DEVICE until dagrt_graph_end is recorded, not run, and
+ * dagrt_graph_launch replays the recorded kernels and copies on the context's stream (the
+ * same device buffers, whatever they hold at replay time). Calls that need the host
+ * during capture (host outputs, dagrt_load_csr, schedule extra-edge buffers, a scratch
+ * buffer that must grow) fail with DAGRT_E_INVAL and leave the capture open: make each
+ * call once before capturing so that its buffers exist. */
+typedef struct dagrt_graph dagrt_graph;
+int dagrt_graph_begin(dagrt_ctx *ctx);
+int dagrt_graph_end(dagrt_ctx *ctx, dagrt_graph **out);
+int dagrt_graph_launch(dagrt_graph *graph);
+void dagrt_graph_free(dagrt_graph *graph);
 
 /* ---------------------------------------------------------------- learned proposer
  * The paper gives the bound of one allocation (Eq.1, Lemma 1, Theorem 1) but no way to

@@ -48,6 +48,9 @@ struct dagrt_ctx {
     int n_sm = 0;
     std::string err;
     int n_batches = 0;
+    // batches, models and graphs alive: dagrt_destroy waits for the last of them
+    int live = 0;
+    bool destroy_pending = false;
     int64_t launches = 0;
     DevicePool pool;
     // side streams: the scheduler's size-class kernels run concurrently, forked from and
@@ -56,6 +59,11 @@ struct dagrt_ctx {
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork = nullptr, join[kSide] = {};
     bool side_ready = false;
+    // stream capture into a CUDA graph (dagrt_graph_begin .. dagrt_graph_end)
+    bool capturing = false;
+    int64_t capture_launch0 = 0;
+    cudaStream_t cap_stream = nullptr;  // captures run here; `stream` is restored at the end
+    cudaStream_t saved_stream = nullptr;
 };
 
 static cudaError_t ensure_side_streams(dagrt_ctx *c) {
@@ -81,7 +89,8 @@ struct Plan {
     int32_t *pflag = nullptr;
     int32_t *status = nullptr;
     int64_t *bound = nullptr;
-    bool chunked = false;  // ci holds this plan's chunks
+    bool chunked = false;  // ci holds this plan's chunks, cut at chunk_rows
+    int chunk_rows = 0;
     ChunkIndex ci = {};
 };
 
@@ -96,14 +105,16 @@ struct dagrt_batch {
     const int32_t *row_ptr = nullptr, *col = nullptr;
     const uint8_t *k64 = nullptr;
     std::vector<std::pair<void *, size_t>> owned;  // pooled device buffers of the batch
-    std::vector<int64_t> h_node_off;
+    std::vector<int64_t> h_node_off, h_edge_off;
+    dagrt_tuning tune = {256, kChunkRows, 4};
     // size classes: warp classes then the CTA class, lists concatenated
     int32_t *lists = nullptr;
     int32_t *counters = nullptr;
     int class_off[kNumWarpClasses + 2] = {0};
     int max_v = 0, big_vcap = 0, big_ecap = 0, big_grid = 0;
-    unsigned char *gws = nullptr;
+    unsigned char *gws = nullptr;  // pooled, gws_cap bytes
     int64_t gws_stride = 0;
+    size_t gws_cap = 0;
     Plan plan[DAGRT_N_VARIANTS];
     int32_t *err = nullptr;  // device error word (bounded waits that gave up)
     // scratch for candidate evaluation
@@ -142,6 +153,14 @@ static int cuda_fail(dagrt_ctx *ctx, cudaError_t e, const char *what) {
                 cudaGetErrorString(e));
 }
 
+// calls that need the host (copies to or from host memory, synchronisation) cannot be
+// recorded into a CUDA graph
+static int refuse_in_capture(dagrt_ctx *ctx, bool needs_host, const char *fn) {
+    if (ctx->capturing && needs_host)
+        return fail(ctx, DAGRT_E_INVAL, "%s: needs the host; not allowed while capturing a graph (use DAGRT_PTR_DEVICE)", fn);
+    return DAGRT_OK;
+}
+
 #define CK(call, what)                                   \
     do {                                                 \
         cudaError_t e_ = (call);                         \
@@ -170,6 +189,9 @@ static void batch_release(dagrt_batch *b) {
     if (b->bscr) b->ctx->pool.put(b->bscr, b->bscr_cap);
     b->bscr = nullptr;
     b->bscr_cap = 0;
+    if (b->gws) b->ctx->pool.put(b->gws, b->gws_cap);
+    b->gws = nullptr;
+    b->gws_cap = 0;
 }
 
 extern "C" {
@@ -193,6 +215,7 @@ int dagrt_create(dagrt_ctx **out, int device, void *cuda_stream) {
 
 int dagrt_set_stream(dagrt_ctx *ctx, void *cuda_stream) {
     if (!ctx) return DAGRT_E_INVAL;
+    if (ctx->capturing) return fail(ctx, DAGRT_E_INVAL, "dagrt_set_stream: not allowed while capturing a graph");
     ctx->stream = (cudaStream_t)cuda_stream;
     return DAGRT_OK;
 }
@@ -204,8 +227,7 @@ int dagrt_sync(dagrt_ctx *ctx) {
     return DAGRT_OK;
 }
 
-void dagrt_destroy(dagrt_ctx *ctx) {
-    if (!ctx) return;
+static void ctx_release(dagrt_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ctx->pool.release_all();
@@ -216,7 +238,22 @@ void dagrt_destroy(dagrt_ctx *ctx) {
         }
         cudaEventDestroy(ctx->fork);
     }
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
+}
+
+// an object of the context went away; the context follows if it was destroyed already
+static void ctx_unref(dagrt_ctx *ctx) {
+    if (--ctx->live == 0 && ctx->destroy_pending) ctx_release(ctx);
+}
+
+void dagrt_destroy(dagrt_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->live > 0) {  // batches, models or graphs still refer to it
+        ctx->destroy_pending = true;
+        return;
+    }
+    ctx_release(ctx);
 }
 
 const char *dagrt_last_error(const dagrt_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -231,8 +268,72 @@ void dagrt_batch_free(dagrt_batch *b) {
     cudaSetDevice(b->ctx->device);
     cudaStreamSynchronize(b->ctx->stream);
     batch_release(b);
-    b->ctx->n_batches--;
+    dagrt_ctx *ctx = b->ctx;
+    ctx->n_batches--;
     delete b;
+    ctx_unref(ctx);
+}
+
+// Size classes for the scheduler: a DAG goes to the smallest warp class whose shared-memory
+// workspace holds its V nodes and E edges, among the classes of at most tune.warp_max_v
+// nodes; the rest go to CTA teams with global workspaces. Each class is ordered by
+// descending node count (longest work first). Host work plus one list upload.
+static int partition_classes(dagrt_batch *b) {
+    dagrt_ctx *ctx = b->ctx;
+    const int n_dags = b->n_dags, max_v = b->max_v;
+    const std::vector<int64_t> &hn = b->h_node_off, &he = b->h_edge_off;
+    int n_warp = 0;  // warp classes enabled
+    while (n_warp < kNumWarpClasses && kWarpClassCap[n_warp] <= b->tune.warp_max_v) n_warp++;
+    std::vector<int32_t> lists(n_dags);
+    std::vector<std::vector<int32_t>> cls(kNumWarpClasses + 1);
+    std::vector<int32_t> order(n_dags);
+    std::vector<int32_t> cnt(max_v + 2, 0);  // counting sort by descending V
+    for (int d = 0; d < n_dags; d++) cnt[max_v - (int)(hn[d + 1] - hn[d])]++;
+    for (int i = 1; i < (int)cnt.size(); i++) cnt[i] += cnt[i - 1];
+    for (int d = n_dags - 1; d >= 0; d--) order[--cnt[max_v - (int)(hn[d + 1] - hn[d])]] = d;
+    int big_v = 0;
+    int64_t big_e = 0;
+    for (int d : order) {
+        const int v = (int)(hn[d + 1] - hn[d]);
+        const int64_t ed = he[d + 1] - he[d];
+        int c = 0;
+        while (c < n_warp && (v > kWarpClassCap[c] || ed > (int64_t)kEdgesPerNode * kWarpClassCap[c])) c++;
+        if (c == n_warp) c = kNumWarpClasses;
+        cls[c].push_back(d);
+        if (c == kNumWarpClasses) {
+            big_v = std::max(big_v, v);
+            big_e = std::max(big_e, ed);
+        }
+    }
+    int off = 0;
+    for (int c = 0; c <= kNumWarpClasses; c++) {
+        b->class_off[c] = off;
+        std::copy(cls[c].begin(), cls[c].end(), lists.begin() + off);
+        off += (int)cls[c].size();
+    }
+    b->class_off[kNumWarpClasses + 1] = off;
+    b->big_vcap = big_v;
+    b->big_ecap = (int)big_e;
+    if (n_dags > 0)
+        CK(cudaMemcpyAsync(b->lists, lists.data(), 4 * n_dags, cudaMemcpyHostToDevice, ctx->stream), "copy class lists");
+    const int n_big = b->class_off[kNumWarpClasses + 1] - b->class_off[kNumWarpClasses];
+    if (n_big > 0) {
+        b->big_grid = std::min(sched_cta_grid(ctx->n_sm), n_big);
+        b->gws_stride = sched_ws_bytes(b->big_vcap, b->big_ecap);
+        const size_t need = (size_t)b->gws_stride * b->big_grid;
+        if (need > b->gws_cap) {
+            if (b->gws) ctx->pool.put(b->gws, b->gws_cap);
+            b->gws = nullptr;
+            b->gws_cap = 0;
+            void *g = nullptr;
+            CK(ctx->pool.get(&g, need), "allocate large-DAG workspace");
+            b->gws = (unsigned char *)g;
+            b->gws_cap = (need + 255) / 256 * 256;
+        }
+    }
+    // the lists upload reads `lists` asynchronously: wait before it goes out of scope
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return DAGRT_OK;
 }
 
 int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, const int64_t *edge_off,
@@ -242,6 +343,7 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
     if (!out) return fail(ctx, DAGRT_E_INVAL, "dagrt_load_csr: out is NULL");
     *out = nullptr;
     if (flags & ~DAGRT_PTR_DEVICE) return fail(ctx, DAGRT_E_INVAL, "dagrt_load_csr: unknown flags 0x%x", flags);
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_load_csr")) return rc;
     if (n_dags < 0) return fail(ctx, DAGRT_E_INVAL, "dagrt_load_csr: n_dags < 0");
     if (M < 1 || M > DAGRT_MAX_M) return fail(ctx, DAGRT_E_INVAL, "dagrt_load_csr: M=%d outside [1, %d]", M, DAGRT_MAX_M);
     if (!node_off || !edge_off) return fail(ctx, DAGRT_E_INVAL, "dagrt_load_csr: NULL offsets");
@@ -317,57 +419,16 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
         b->k64 = dk;
     }
 
-    // size classes, each ordered by descending node count (longest work first)
-    std::vector<int32_t> lists(n_dags);
-    {
-        std::vector<std::vector<int32_t>> cls(kNumWarpClasses + 1);
-        std::vector<int32_t> order(n_dags);
-        std::vector<int32_t> cnt(max_v + 2, 0);  // counting sort by descending V
-        for (int d = 0; d < n_dags; d++) cnt[max_v - (int)(hn[d + 1] - hn[d])]++;
-        for (int i = 1; i < (int)cnt.size(); i++) cnt[i] += cnt[i - 1];
-        for (int d = n_dags - 1; d >= 0; d--) order[--cnt[max_v - (int)(hn[d + 1] - hn[d])]] = d;
-        int big_v = 0;
-        int64_t big_e = 0;
-        for (int d : order) {
-            const int v = (int)(hn[d + 1] - hn[d]);
-            const int64_t ed = he[d + 1] - he[d];
-            int c = 0;  // the smallest class whose workspace holds V nodes and E edges
-            while (c < kNumWarpClasses && (v > kWarpClassCap[c] || ed > (int64_t)kEdgesPerNode * kWarpClassCap[c])) c++;
-            cls[c].push_back(d);
-            if (c == kNumWarpClasses) {
-                big_v = std::max(big_v, v);
-                big_e = std::max(big_e, ed);
-            }
-        }
-        b->big_ecap = (int)big_e;
-        int off = 0;
-        for (int c = 0; c <= kNumWarpClasses; c++) {
-            b->class_off[c] = off;
-            std::copy(cls[c].begin(), cls[c].end(), lists.begin() + off);
-            off += (int)cls[c].size();
-        }
-        b->class_off[kNumWarpClasses + 1] = off;
-        b->big_vcap = big_v;
-    }
+    b->h_edge_off = he;
     if ((e = batch_alloc(b, &b->lists, n_dags)) != cudaSuccess ||
         (e = batch_alloc(b, &b->counters, 8)) != cudaSuccess || (e = batch_alloc(b, &b->err, 1)) != cudaSuccess ||
         (e = cudaMemsetAsync(b->err, 0, sizeof(int32_t), ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "allocate class lists"));
-    if (n_dags > 0 &&
-        (e = cudaMemcpyAsync(b->lists, lists.data(), 4 * n_dags, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
-        return bail(cuda_fail(ctx, e, "copy class lists"));
-    const int n_big = b->class_off[kNumWarpClasses + 1] - b->class_off[kNumWarpClasses];
-    if (n_big > 0) {
-        b->big_grid = std::min(sched_cta_grid(ctx->n_sm), n_big);
-        b->gws_stride = sched_ws_bytes(b->big_vcap, b->big_ecap);
-        unsigned char *g;
-        if ((e = batch_alloc(b, &g, (size_t)b->gws_stride * b->big_grid)) != cudaSuccess)
-            return bail(cuda_fail(ctx, e, "allocate large-DAG workspace"));
-        b->gws = g;
-    }
+    if (int rc = partition_classes(b)) return bail(rc);
     // host copies must be complete before the caller may reuse its buffers
     if (!dev && (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "synchronize"));
     ctx->n_batches++;
+    ctx->live++;
     *out = b;
     return DAGRT_OK;
 }
@@ -404,25 +465,30 @@ static int ensure_plan(dagrt_batch *b, int variant) {
 static int ensure_chunks(dagrt_batch *b, int variant) {
     dagrt_ctx *ctx = b->ctx;
     Plan &p = b->plan[variant];
-    if (p.chunked) return DAGRT_OK;
-    if (!p.ci.chunk) {
+    if (p.chunked && p.chunk_rows == b->tune.chunk_rows) return DAGRT_OK;
+    if (!p.ci.chunk) {  // sized for the smallest chunk_rows, so a retune never reallocates
         cudaError_t e;
         if ((e = batch_alloc(b, &p.ci.chunk, (size_t)(2 * b->total_nodes))) != cudaSuccess ||
             (e = batch_alloc(b, &p.ci.nchunk, (size_t)b->n_dags)) != cudaSuccess ||
             (e = batch_alloc(b, &p.ci.cpre, (size_t)b->n_dags + 1)) != cudaSuccess ||
-            (e = batch_alloc(b, &p.ci.item, (size_t)chunk_items_bound(b->total_nodes, b->n_dags))) != cudaSuccess)
+            (e = batch_alloc(b, &p.ci.item, (size_t)chunk_items_bound(b->total_nodes, b->n_dags, kMinChunkRows))) !=
+                cudaSuccess)
             return cuda_fail(ctx, e, "allocate plan chunks");
     }
-    CK(bound_build_chunks(b->n_dags, b->node_off, p.rows, p.nrows, p.status, p.ci, ctx->n_sm, ctx->stream),
+    CK(bound_build_chunks(b->n_dags, b->node_off, p.rows, p.nrows, p.status, p.ci, b->tune.chunk_rows, ctx->n_sm,
+                          ctx->stream),
        "build plan chunks");
     ctx->launches += 3;
-    p.chunked = true;
+    // a capture only records the build: an eager call after it must build again
+    p.chunked = !ctx->capturing;
+    p.chunk_rows = b->tune.chunk_rows;
     return DAGRT_OK;
 }
 
 static int ensure_bscr(dagrt_batch *b, size_t bytes) {
     dagrt_ctx *ctx = b->ctx;
     if (b->bscr_cap >= bytes) return DAGRT_OK;
+    if (ctx->capturing) return fail(ctx, DAGRT_E_INVAL, "scratch must grow during graph capture: make the call once before capturing");
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     if (b->bscr) ctx->pool.put(b->bscr, b->bscr_cap);
     b->bscr = nullptr;
@@ -438,6 +504,7 @@ static int ensure_bscr(dagrt_batch *b, size_t bytes) {
 static int ensure_tmp(dagrt_batch *b, size_t bytes) {
     dagrt_ctx *ctx = b->ctx;
     if (b->tmp_cap >= bytes) return DAGRT_OK;
+    if (ctx->capturing) return fail(ctx, DAGRT_E_INVAL, "scratch must grow during graph capture: make the call once before capturing");
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     if (b->tmp) ctx->pool.put(b->tmp, b->tmp_cap);
     b->tmp = nullptr;
@@ -454,6 +521,8 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
     if (variant < 0 || variant >= DAGRT_N_VARIANTS)
         return fail(ctx, DAGRT_E_INVAL, "dagrt_schedule: unknown variant %d", variant);
     if (flags & ~DAGRT_PTR_DEVICE) return fail(ctx, DAGRT_E_INVAL, "dagrt_schedule: unknown flags 0x%x", flags);
+    if (int rc = refuse_in_capture(ctx, !(flags & DAGRT_PTR_DEVICE) || (out && out->extra_off), "dagrt_schedule"))
+        return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     int rc = ensure_plan(b, variant);
     if (rc) return rc;
@@ -583,6 +652,7 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
     if (!b) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (flags & ~DAGRT_PTR_DEVICE) return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: unknown flags 0x%x", flags);
+    if (int rc = refuse_in_capture(ctx, !(flags & DAGRT_PTR_DEVICE), "dagrt_bound")) return rc;
     if (n_variants < 1 || n_variants > kMaxVariantsPerCall || !variant_ids)
         return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: n_variants must be in [1, %d]", kMaxVariantsPerCall);
     if (n_alloc < 1) return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: n_alloc < 1");
@@ -646,7 +716,7 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
     }
     ChunkArgs ch;
     std::memset(&ch, 0, sizeof ch);
-    const bool items = bound_chunk_eligible(a, b->total_nodes);
+    const bool items = bound_chunk_eligible(a, b->total_nodes, b->tune.chunk_rows);
     if (items) {
         for (int i = 0; i < n_variants; i++) {
             const int v = variant_ids[i];
@@ -657,7 +727,7 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
             ch.cpre[i] = b->plan[v].ci.cpre;
             ch.item[i] = b->plan[v].ci.item;
         }
-        int rc = ensure_bscr(b, bound_chunk_scratch(b->n_dags, b->total_nodes, n_variants, n_alloc));
+        int rc = ensure_bscr(b, bound_chunk_scratch(b->n_dags, b->total_nodes, n_variants, n_alloc, b->tune.chunk_rows));
         if (rc) return rc;
         const size_t per_dag = (4 * nd + 255) / 256 * 256;
         char *t = (char *)b->bscr;
@@ -666,6 +736,7 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
         t += 256;
         ch.wide_list = (int32_t *)t;
         ch.partial = (int32_t *)(t + per_dag);
+        ch.warps = b->tune.item_warps;
     }
     int nl = 0;
     CK(bound_launch(a, items ? &ch : nullptr, ctx->n_sm, ctx->stream, &nl), "launch bound kernel");
@@ -688,6 +759,7 @@ extern "C" int dagrt_search(dagrt_batch *b, const dagrt_search_cfg *cfg, int64_t
     dagrt_ctx *ctx = b->ctx;
     if (!cfg) return fail(ctx, DAGRT_E_INVAL, "dagrt_search: cfg is NULL");
     if (flags & ~DAGRT_PTR_DEVICE) return fail(ctx, DAGRT_E_INVAL, "dagrt_search: unknown flags 0x%x", flags);
+    if (int rc = refuse_in_capture(ctx, !(flags & DAGRT_PTR_DEVICE), "dagrt_search")) return rc;
     if (cfg->n_variants < 1 || cfg->n_variants > kMaxVariantsPerCall || !cfg->variant_ids)
         return fail(ctx, DAGRT_E_INVAL, "dagrt_search: n_variants must be in [1, %d]", kMaxVariantsPerCall);
     if (cfg->n_alloc < 1 || (int64_t)cfg->n_variants * cfg->n_alloc > (1 << 20))
@@ -831,7 +903,7 @@ static int gnn_prepare(dagrt_batch *b, bool train) {
         CK(gnn_features(b->n_dags, b->node_off, b->wcet, b->k64, G.level, G.wanc, G.m, graph_of(b), G.x, ctx->n_sm,
                         ctx->stream), "node features");
         ctx->launches += 3;
-        G.graph = true;
+        G.graph = !ctx->capturing;  // a capture only records the build
     }
     if (train && !G.train) {
         if ((e = batch_alloc(b, &G.dlogits, N * kMaxLevels)) != cudaSuccess ||
@@ -910,20 +982,24 @@ extern "C" int dagrt_model_create(dagrt_ctx *ctx, int32_t n_levels, const uint8_
         (e = gnn_refresh(md->p, md->wt, md->wb, st)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "initialise model"));
     *out = md;
+    ctx->live++;
     return DAGRT_OK;
 }
 
 extern "C" void dagrt_model_free(dagrt_model *md) {
     if (!md) return;
-    cudaSetDevice(md->ctx->device);
-    cudaStreamSynchronize(md->ctx->stream);
-    for (auto &pb : md->owned) md->ctx->pool.put(pb.first, pb.second);
+    dagrt_ctx *ctx = md->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &pb : md->owned) ctx->pool.put(pb.first, pb.second);
     delete md;
+    ctx_unref(ctx);
 }
 
 extern "C" int dagrt_model_params(dagrt_model *md, float *get, const float *set) {
     if (!md) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = md->ctx;
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_model_params")) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     const size_t bytes = ParamLayout::total * 4;
     if (set) {
@@ -939,6 +1015,7 @@ extern "C" int dagrt_model_logits(dagrt_batch *b, dagrt_model *md, float *logits
     if (!b || !md) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (md->ctx != ctx) return fail(ctx, DAGRT_E_INVAL, "dagrt_model_logits: model of another context");
+    if (int rc = refuse_in_capture(ctx, !(flags & DAGRT_PTR_DEVICE), "dagrt_model_logits")) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     int rc = gnn_prepare(b, false);
     if (rc) return rc;
@@ -998,6 +1075,7 @@ static int gnn_grad(dagrt_batch *b, dagrt_model *md, const int8_t *labels, float
 extern "C" int dagrt_model_grad(dagrt_batch *b, dagrt_model *md, const int8_t *labels, float *grads, float *loss) {
     if (!b || !md || !labels) return b ? fail(b->ctx, DAGRT_E_INVAL, "dagrt_model_grad: NULL argument") : DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_model_grad")) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     int rc = gnn_grad(b, md, labels, loss);
     if (rc) return rc;
@@ -1017,6 +1095,7 @@ extern "C" int dagrt_model_grad(dagrt_batch *b, dagrt_model *md, const int8_t *l
 extern "C" int dagrt_train_step(dagrt_batch *b, dagrt_model *md, const int8_t *labels, float lr, float *loss) {
     if (!b || !md || !labels) return b ? fail(b->ctx, DAGRT_E_INVAL, "dagrt_train_step: NULL argument") : DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_train_step")) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     int rc = gnn_grad(b, md, labels, loss);
     if (rc) return rc;
@@ -1035,6 +1114,7 @@ extern "C" int dagrt_propose(dagrt_batch *b, dagrt_model *md, int32_t k, int64_t
     if (md->ctx != ctx) return fail(ctx, DAGRT_E_INVAL, "dagrt_propose: model of another context");
     if (k < 1 || k > 16) return fail(ctx, DAGRT_E_INVAL, "dagrt_propose: k must be in [1, 16]");
     if (flags & ~DAGRT_PTR_DEVICE) return fail(ctx, DAGRT_E_INVAL, "dagrt_propose: unknown flags 0x%x", flags);
+    if (int rc = refuse_in_capture(ctx, !(flags & DAGRT_PTR_DEVICE), "dagrt_propose")) return rc;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     int rc = gnn_prepare(b, false);
     if (rc) return rc;
@@ -1097,4 +1177,209 @@ extern "C" int dagrt_propose(dagrt_batch *b, dagrt_model *md, int32_t k, int64_t
     CK(cudaStreamSynchronize(st), "synchronize");
     if (err) return fail(ctx, err, "a wait did not complete in time");
     return DAGRT_OK;
+}
+
+// ------------------------------------------------------------------ batching controls
+extern "C" int dagrt_get_tuning(const dagrt_batch *b, dagrt_tuning *out) {
+    if (!b || !out) return DAGRT_E_INVAL;
+    *out = b->tune;
+    return DAGRT_OK;
+}
+
+extern "C" int dagrt_set_tuning(dagrt_batch *b, const dagrt_tuning *t) {
+    if (!b) return DAGRT_E_INVAL;
+    dagrt_ctx *ctx = b->ctx;
+    if (!t) return fail(ctx, DAGRT_E_INVAL, "dagrt_set_tuning: NULL");
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_set_tuning")) return rc;
+    const int w = t->warp_max_v;
+    if (w != 0 && w != 64 && w != 128 && w != 192 && w != 256)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_set_tuning: warp_max_v must be 0, 64, 128, 192 or 256");
+    if (t->chunk_rows < kMinChunkRows || t->chunk_rows > 256)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_set_tuning: chunk_rows must be in [%d, 256]", kMinChunkRows);
+    if (t->item_warps < 1 || t->item_warps > 8)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_set_tuning: item_warps must be in [1, 8]");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const bool repart = t->warp_max_v != b->tune.warp_max_v;
+    b->tune = *t;
+    if (repart) {
+        CK(cudaStreamSynchronize(ctx->stream), "synchronize");  // the lists may be in use
+        return partition_classes(b);
+    }
+    return DAGRT_OK;
+}
+
+namespace {
+float median_of(std::vector<float> v) {
+    std::sort(v.begin(), v.end());
+    return v.empty() ? 0.f : v[v.size() / 2];
+}
+}  // namespace
+
+// time `call` reps times after one warm-up (CUDA events on the context's stream)
+template <class F>
+static int time_call(dagrt_ctx *ctx, int reps, F call, float *ms) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    std::vector<float> t;
+    int rc = DAGRT_OK;
+    for (int r = 0; r <= reps && rc == DAGRT_OK; r++) {
+        cudaEventRecord(e0, ctx->stream);
+        rc = call();
+        cudaEventRecord(e1, ctx->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_fail(ctx, cudaGetLastError(), "time call");
+        float x = 0.f;
+        cudaEventElapsedTime(&x, e0, e1);
+        if (r > 0) t.push_back(x);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = median_of(t);
+    return rc;
+}
+
+extern "C" int dagrt_autotune_schedule(dagrt_batch *b, int32_t variant, int32_t reps, dagrt_tuning *chosen,
+                                       float *best_ms) {
+    if (!b) return DAGRT_E_INVAL;
+    dagrt_ctx *ctx = b->ctx;
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_autotune_schedule")) return rc;
+    if (reps < 1) return fail(ctx, DAGRT_E_INVAL, "dagrt_autotune_schedule: reps < 1");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    dagrt_tuning best = b->tune;
+    float bt = -1.f;
+    for (int w : {64, 128, 192, 256}) {
+        dagrt_tuning t = b->tune;
+        t.warp_max_v = w;
+        int rc = dagrt_set_tuning(b, &t);
+        if (rc) return rc;
+        dagrt_schedule_out o;
+        std::memset(&o, 0, sizeof o);
+        float ms = 0.f;
+        rc = time_call(ctx, reps, [&]() { return dagrt_schedule(b, variant, &o, DAGRT_PTR_DEVICE); }, &ms);
+        if (rc) return rc;
+        if (bt < 0.f || ms < bt) {
+            bt = ms;
+            best = t;
+        }
+    }
+    int rc = dagrt_set_tuning(b, &best);
+    if (rc) return rc;
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = bt;
+    return DAGRT_OK;
+}
+
+extern "C" int dagrt_autotune_bound(dagrt_batch *b, int32_t n_variants, const int32_t *variant_ids, int32_t n_alloc,
+                                    const uint8_t *m_alloc, int64_t cand_stride, int32_t reps, dagrt_tuning *chosen,
+                                    float *best_ms) {
+    if (!b) return DAGRT_E_INVAL;
+    dagrt_ctx *ctx = b->ctx;
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_autotune_bound")) return rc;
+    if (reps < 1) return fail(ctx, DAGRT_E_INVAL, "dagrt_autotune_bound: reps < 1");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    dagrt_tuning best = b->tune;
+    float bt = -1.f;
+    const bool tunable = n_alloc > 0 && n_alloc % 64 == 0;
+    std::vector<std::pair<int, int>> grid;
+    if (tunable) {
+        for (int cr : {16, 24, 32, 48})
+            for (int wp : {2, 4, 8}) grid.emplace_back(cr, wp);
+    } else {
+        grid.emplace_back(b->tune.chunk_rows, b->tune.item_warps);
+    }
+    for (auto &g : grid) {
+        dagrt_tuning t = b->tune;
+        t.chunk_rows = g.first;
+        t.item_warps = g.second;
+        int rc = dagrt_set_tuning(b, &t);
+        if (rc) return rc;
+        float ms = 0.f;
+        rc = time_call(ctx, reps, [&]() {
+            return dagrt_bound(b, n_variants, variant_ids, n_alloc, m_alloc, cand_stride, nullptr, nullptr, nullptr,
+                               DAGRT_PTR_DEVICE);
+        }, &ms);
+        if (rc) return rc;
+        if (bt < 0.f || ms < bt) {
+            bt = ms;
+            best = t;
+        }
+    }
+    int rc = dagrt_set_tuning(b, &best);
+    if (rc) return rc;
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = bt;
+    return DAGRT_OK;
+}
+
+// ------------------------------------------------------------------ CUDA graphs
+struct dagrt_graph {
+    dagrt_ctx *ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+};
+
+extern "C" int dagrt_graph_begin(dagrt_ctx *ctx) {
+    if (!ctx) return DAGRT_E_INVAL;
+    if (ctx->capturing) return fail(ctx, DAGRT_E_INVAL, "dagrt_graph_begin: already capturing");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(ensure_side_streams(ctx), "create side streams");  // not during capture
+    // the legacy default stream cannot be captured: record on a private stream instead
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "create capture stream");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+    ctx->saved_stream = ctx->stream;
+    ctx->stream = ctx->cap_stream;
+    ctx->capturing = true;
+    ctx->capture_launch0 = ctx->launches;
+    return DAGRT_OK;
+}
+
+extern "C" int dagrt_graph_end(dagrt_ctx *ctx, dagrt_graph **out) {
+    if (!ctx) return DAGRT_E_INVAL;
+    if (!out) return fail(ctx, DAGRT_E_INVAL, "dagrt_graph_end: out is NULL");
+    *out = nullptr;
+    if (!ctx->capturing) return fail(ctx, DAGRT_E_INVAL, "dagrt_graph_end: not capturing");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->stream = ctx->saved_stream;
+    ctx->capturing = false;
+    const int64_t n = ctx->launches - ctx->capture_launch0;
+    ctx->launches = ctx->capture_launch0;  // recorded, not run
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ctx, e, "instantiate graph");
+    }
+    dagrt_graph *gr = new dagrt_graph();
+    gr->ctx = ctx;
+    gr->graph = g;
+    gr->exec = x;
+    gr->launches = n;
+    *out = gr;
+    ctx->live++;
+    return DAGRT_OK;
+}
+
+extern "C" int dagrt_graph_launch(dagrt_graph *g) {
+    if (!g) return DAGRT_E_INVAL;
+    dagrt_ctx *ctx = g->ctx;
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_graph_launch")) return rc;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaGraphLaunch(g->exec, ctx->stream), "launch graph");
+    ctx->launches += g->launches;
+    return DAGRT_OK;
+}
+
+extern "C" void dagrt_graph_free(dagrt_graph *g) {
+    if (!g) return;
+    cudaSetDevice(g->ctx->device);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    dagrt_ctx *ctx = g->ctx;
+    delete g;
+    ctx_unref(ctx);
 }

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
 
 // ------------------------------------------------------------------ balanced work items
 constexpr int kSubRows = 32;     // plan rows staged per load phase of a work item
-constexpr int kChunkWarps = 4;   // warps per CTA of the work-item kernel
+constexpr int kMaxItemWarps = 8;  // warps per CTA of the work-item kernel: ChunkArgs::warps <= this
 // per warp: two staging buffers (candidate bytes + plan rows) and one {C, m} table
 constexpr int kStageBytes = kSubRows * 64 + kSubRows * 16;
 constexpr int kWarpBytes = 2 * kStageBytes + kSubRows * 9 * 8;
@@ -319,11 +319,11 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Chunk starts of every DAG of one plan (one warp per DAG). Chunk 0 starts at row 0; a new
-// chunk starts at the first row p >= start + kChunkRows whose previous row ends a group.
+// chunk starts at the first row p >= start + chunk_rows whose previous row ends a group.
 // The group-end bits of 32 rows at a time come from one ballot; every lane walks the same
 // mask, lane 0 writes.
 __global__ void k_plan_chunks(int32_t n_dags, const int64_t *node_off, const uint4 *plan, const int32_t *nrows,
-                              const int32_t *status, int32_t *chunk, int32_t *nchunk) {
+                              const int32_t *status, int32_t *chunk, int32_t *nchunk, int chunk_rows) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dags; d += warps) {
@@ -339,7 +339,7 @@ __global__ void k_plan_chunks(int32_t n_dags, const int64_t *node_off, const uin
             const bool endg = r < rows && (plan[rbase + r].z >> 24) != 0;
             const uint32_t mask = __ballot_sync(FULL, endg);
             for (;;) {
-                const int lo = cur + kChunkRows - 1 - base;  // bit i gives the start p = base + i + 1
+                const int lo = cur + chunk_rows - 1 - base;  // bit i gives the start p = base + i + 1
                 if (lo > 31) break;
                 const uint32_t mm = lo <= 0 ? mask : (mask & (~0u << lo));
                 if (!mm) break;
@@ -402,29 +402,30 @@ __global__ void k_fill_items(int32_t n_dags, const int64_t *node_off, const int3
 }
 
 cudaError_t bound_build_chunks(int32_t n_dags, const int64_t *node_off, const uint4 *plan, const int32_t *nrows,
-                               const int32_t *status, const ChunkIndex &ci, int n_sm, cudaStream_t st) {
+                               const int32_t *status, const ChunkIndex &ci, int chunk_rows, int n_sm, cudaStream_t st) {
     if (n_dags == 0) return cudaMemsetAsync(ci.cpre, 0, sizeof(int32_t), st);
     int grid = (n_dags + 7) / 8;
     if (grid > 16 * n_sm) grid = 16 * n_sm;
-    k_plan_chunks<<<grid, 256, 0, st>>>(n_dags, node_off, plan, nrows, status, ci.chunk, ci.nchunk);
+    k_plan_chunks<<<grid, 256, 0, st>>>(n_dags, node_off, plan, nrows, status, ci.chunk, ci.nchunk, chunk_rows);
     k_scan_excl<<<1, 1024, 0, st>>>(n_dags, ci.nchunk, ci.cpre);
     k_fill_items<<<grid, 256, 0, st>>>(n_dags, node_off, nrows, ci.chunk, ci.nchunk, ci.cpre, ci.item);
     return cudaGetLastError();
 }
 
-static int64_t chunk_items_call(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc) {
-    return (int64_t)n_variants * chunk_items_bound(total_nodes, n_dags) * (n_alloc / 64);
+static int64_t chunk_items_call(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc,
+                                int chunk_rows) {
+    return (int64_t)n_variants * chunk_items_bound(total_nodes, n_dags, chunk_rows) * (n_alloc / 64);
 }
 
-bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes) {
+bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes, int chunk_rows) {
     return !a.gen && a.n_alloc % 64 == 0 && a.n_dags > 0 && !a.dag_list &&
-           chunk_items_call(a.n_dags, total_nodes, a.n_variants, a.n_alloc) < (1ll << 30) &&
+           chunk_items_call(a.n_dags, total_nodes, a.n_variants, a.n_alloc, chunk_rows) < (1ll << 30) &&
            2 * total_nodes < (1ll << 31);
 }
 
-size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc) {
+size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc, int chunk_rows) {
     return 256 + ((size_t)(4 * n_dags + 255) / 256 * 256) +
-           (size_t)chunk_items_call(n_dags, total_nodes, n_variants, n_alloc) * 64 * 4;
+           (size_t)chunk_items_call(n_dags, total_nodes, n_variants, n_alloc, chunk_rows) * 64 * 4;
 }
 
 // After the work items (one CTA per DAG): a DAG whose sums fit 32 bits gets its candidate
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(256) k_bound_finish(BoundArgs a, ChunkArgs ch)
 // of one row adds its C directly. Each item writes 64 partial sums; k_bound_finish adds
 // them up per candidate once every item is done.
 template <bool CHECK_M>
-__global__ void __launch_bounds__(kChunkWarps * 32) k_bound_items(BoundArgs a, ChunkArgs ch) {
+__global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a, ChunkArgs ch) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ int64_t s_cum[kMaxVariantsPerCall + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -635,14 +636,15 @@ cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cuda
         // the item counter is zero here: set when the scratch was allocated, and reset by
         // k_bound_finish at the end of every call
         cudaError_t e;
-        const int smem = kChunkWarps * kWarpBytes;
+        const int warps = ch->warps < 1 ? 1 : (ch->warps > kMaxItemWarps ? kMaxItemWarps : ch->warps);
+        const int smem = warps * kWarpBytes;
         auto kern = a.M < 128 ? k_bound_items<true> : k_bound_items<false>;
         int per_sm = 0;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChunkWarps * 32, smem);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxItemWarps * kWarpBytes);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
-        kern<<<per_sm * n_sm, kChunkWarps * 32, smem, st>>>(a, *ch);
+        kern<<<per_sm * n_sm, warps * 32, smem, st>>>(a, *ch);
         const int g = a.n_dags < 16 * n_sm ? a.n_dags : 16 * n_sm;
         k_bound_finish<<<g, 256, 0, st>>>(a, *ch);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -60,11 +60,12 @@ __host__ __device__ inline int gen_level(uint64_t seed, int64_t d, int64_t c, in
 // cut at a group end, block of 64 candidates): the bound is a sum over groups (Theorem 1),
 // so chunks evaluate independently and their partial sums add up. Chunks are a property of
 // the plan and are built once per plan.
-constexpr int kChunkRows = 24;
+constexpr int kChunkRows = 24;     // default target rows per work item
+constexpr int kMinChunkRows = 8;
 
-// upper bound on the chunks of one plan (every chunk but a DAG's last has >= kChunkRows rows)
-inline int64_t chunk_items_bound(int64_t total_nodes, int32_t n_dags) {
-    return 2 * total_nodes / kChunkRows + n_dags + 1;
+// upper bound on the chunks of one plan (every chunk but a DAG's last has >= chunk_rows rows)
+inline int64_t chunk_items_bound(int64_t total_nodes, int32_t n_dags, int chunk_rows) {
+    return 2 * total_nodes / chunk_rows + n_dags + 1;
 }
 
 struct ChunkIndex {  // device arrays of one plan
@@ -75,7 +76,7 @@ struct ChunkIndex {  // device arrays of one plan
 };
 
 cudaError_t bound_build_chunks(int32_t n_dags, const int64_t *node_off, const uint4 *plan, const int32_t *nrows,
-                               const int32_t *status, const ChunkIndex &ci, int n_sm, cudaStream_t st);
+                               const int32_t *status, const ChunkIndex &ci, int chunk_rows, int n_sm, cudaStream_t st);
 
 struct ChunkArgs {
     const int32_t *chunk[kMaxVariantsPerCall], *nchunk[kMaxVariantsPerCall], *cpre[kMaxVariantsPerCall];
@@ -84,13 +85,14 @@ struct ChunkArgs {
     int32_t *wide_n;              // DAGs left to the 64-bit kernel ...
     int32_t *wide_list;           // ... and their ids [n_dags]
     int32_t *partial;             // [items * 64] partial bounds
+    int32_t warps;                // warps per CTA of the work-item kernel
 };
 
 // scratch bytes the balanced path needs for a call (counters, wide list, partials)
-size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc);
+size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc, int chunk_rows);
 // the call can take the balanced path (materialised candidates, n_alloc % 64 == 0, and few
 // enough work items for 32-bit item ids)
-bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes);
+bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes, int chunk_rows);
 
 // Enqueue the bound kernels; *launches receives the number of kernels enqueued. With ch
 // (and an eligible call), the balanced path takes the DAGs whose sums fit 32 bits.

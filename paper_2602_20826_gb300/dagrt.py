@@ -78,6 +78,23 @@ dagrt_train_step = _sig("dagrt_train_step", C.c_int, [_vp, _vp, _vp, C.c_float, 
 dagrt_propose = _sig("dagrt_propose", C.c_int, [_vp, _vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, C.c_uint32])
 
 
+class dagrt_tuning(C.Structure):
+    _fields_ = [("warp_max_v", C.c_int32), ("chunk_rows", C.c_int32), ("item_warps", C.c_int32)]
+
+
+dagrt_get_tuning = _sig("dagrt_get_tuning", C.c_int, [_vp, C.POINTER(dagrt_tuning)])
+dagrt_set_tuning = _sig("dagrt_set_tuning", C.c_int, [_vp, C.POINTER(dagrt_tuning)])
+dagrt_autotune_schedule = _sig("dagrt_autotune_schedule", C.c_int,
+                               [_vp, C.c_int32, C.c_int32, C.POINTER(dagrt_tuning), C.POINTER(C.c_float)])
+dagrt_autotune_bound = _sig("dagrt_autotune_bound", C.c_int,
+                            [_vp, C.c_int32, C.POINTER(C.c_int32), C.c_int32, _vp, C.c_int64, C.c_int32,
+                             C.POINTER(dagrt_tuning), C.POINTER(C.c_float)])
+dagrt_graph_begin = _sig("dagrt_graph_begin", C.c_int, [_vp])
+dagrt_graph_end = _sig("dagrt_graph_end", C.c_int, [_vp, C.POINTER(_vp)])
+dagrt_graph_launch = _sig("dagrt_graph_launch", C.c_int, [_vp])
+dagrt_graph_free = _sig("dagrt_graph_free", None, [_vp])
+
+
 class DagrtError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"dagrt error {code}: {msg}")
@@ -142,6 +159,14 @@ class Context:
         except Exception:
             pass
 
+    def graph_begin(self):
+        self.check(dagrt_graph_begin(self.h))
+
+    def graph_end(self) -> "Graph":
+        g = _vp()
+        self.check(dagrt_graph_end(self.h, C.byref(g)))
+        return Graph(self, g)
+
     def load(self, arrays, M: int | None = None) -> "LoadedBatch":
         """Load a batch: a workloads.Batch (host numpy arrays, copied) or a dict of torch
         CUDA tensors with keys node_off, edge_off, row_ptr, col, wcet, k64 (used in place)."""
@@ -164,6 +189,27 @@ class Context:
         return LoadedBatch(self, h, n, M, keep=a)
 
 
+class Graph:
+    """A recorded sequence of device-side library calls (dagrt_graph_*)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def launch(self):
+        self.ctx.check(dagrt_graph_launch(self.h))
+
+    def free(self):
+        if self.h:
+            dagrt_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 class LoadedBatch:
     def __init__(self, ctx: Context, h, n_dags: int, M: int, keep=None):
         self.ctx, self.h, self.n_dags, self.M = ctx, h, n_dags, M
@@ -180,6 +226,30 @@ class LoadedBatch:
             self.free()
         except Exception:
             pass
+
+    def tuning(self) -> dict:
+        t = dagrt_tuning()
+        self.ctx.check(dagrt_get_tuning(self.h, C.byref(t)))
+        return {"warp_max_v": t.warp_max_v, "chunk_rows": t.chunk_rows, "item_warps": t.item_warps}
+
+    def set_tuning(self, **kw):
+        cur = self.tuning()
+        cur.update(kw)
+        t = dagrt_tuning(int(cur["warp_max_v"]), int(cur["chunk_rows"]), int(cur["item_warps"]))
+        self.ctx.check(dagrt_set_tuning(self.h, C.byref(t)))
+
+    def autotune_schedule(self, variant: int = VAR_PAPER, reps: int = 3):
+        t, ms = dagrt_tuning(), C.c_float(0)
+        self.ctx.check(dagrt_autotune_schedule(self.h, int(variant), int(reps), C.byref(t), C.byref(ms)))
+        return {"warp_max_v": t.warp_max_v, "chunk_rows": t.chunk_rows, "item_warps": t.item_warps}, ms.value
+
+    def autotune_bound(self, variant_ids, n_alloc: int, m_alloc, cand_stride: int, reps: int = 3):
+        """m_alloc: a torch CUDA tensor (device candidates)."""
+        vids = (C.c_int32 * len(variant_ids))(*[int(v) for v in variant_ids])
+        t, ms = dagrt_tuning(), C.c_float(0)
+        self.ctx.check(dagrt_autotune_bound(self.h, len(variant_ids), vids, int(n_alloc), _ptr(m_alloc),
+                                            int(cand_stride), int(reps), C.byref(t), C.byref(ms)))
+        return {"warp_max_v": t.warp_max_v, "chunk_rows": t.chunk_rows, "item_warps": t.item_warps}, ms.value
 
     def schedule(self, variant: int = VAR_PAPER, fields=("bound", "status"), extra_cap=None,
                  out=None, check: bool = True):
