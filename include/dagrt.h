@@ -244,11 +244,15 @@ int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_
  *   chunk_rows  candidate bounds: the plan rows of a DAG are cut into work items of about
  *               this many rows at group ends (Theorem 1's sum splits there); 8 .. 256.
  *               Default 24.
- *   item_warps  candidate bounds: warps per CTA of the work-item kernel, 1 .. 8. Default 4. */
+ *   item_warps  candidate bounds: warps per CTA of the work-item kernel, 1 .. 8. Default 4.
+ *   cta_smem    scheduler: k in 1 .. 4 = CTA teams keep their workspace in shared memory
+ *               while it takes at most 1/k of a CTA's shared memory (smallest large DAGs
+ *               first; k teams then fit per SM), 0 = always in global memory. Default 2. */
 typedef struct {
     int32_t warp_max_v;
     int32_t chunk_rows;
     int32_t item_warps;
+    int32_t cta_smem;
 } dagrt_tuning;
 
 int dagrt_get_tuning(const dagrt_batch *batch, dagrt_tuning *out);
@@ -257,7 +261,7 @@ int dagrt_get_tuning(const dagrt_batch *batch, dagrt_tuning *out);
 int dagrt_set_tuning(dagrt_batch *batch, const dagrt_tuning *t);
 
 /* Autotuner. Times dagrt_schedule(batch, variant) (device outputs) for every warp_max_v
- * in {64, 128, 192, 256}, `reps` times each after one warm-up (CUDA events on the
+ * in {64, 128, 192, 256} x cta_smem in {0, 1, 2, 3, 4}, `reps` times each after one warm-up (CUDA events on the
  * context's stream), keeps the fastest setting in the batch and returns it (*best_ms: its
  * median time). Synchronous. */
 int dagrt_autotune_schedule(dagrt_batch *batch, int32_t variant, int32_t reps, dagrt_tuning *chosen,

@@ -55,7 +55,7 @@ struct dagrt_ctx {
     DevicePool pool;
     // side streams: the scheduler's size-class kernels run concurrently, forked from and
     // joined back into `stream` with events
-    static constexpr int kSide = 5;
+    static constexpr int kSide = 6;
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork = nullptr, join[kSide] = {};
     bool side_ready = false;
@@ -81,6 +81,9 @@ namespace {
 
 constexpr int kNumWarpClasses = 4;
 constexpr int kWarpClassCap[kNumWarpClasses] = {64, 128, 192, 256};
+// classes after the warp classes: CTA teams with a shared-memory workspace, then CTA teams
+// with global workspaces
+constexpr int kClsCtaSmem = kNumWarpClasses, kClsCtaGlobal = kNumWarpClasses + 1, kNumClasses = kNumWarpClasses + 2;
 
 struct Plan {
     bool valid = false;
@@ -106,12 +109,13 @@ struct dagrt_batch {
     const uint8_t *k64 = nullptr;
     std::vector<std::pair<void *, size_t>> owned;  // pooled device buffers of the batch
     std::vector<int64_t> h_node_off, h_edge_off;
-    dagrt_tuning tune = {256, kChunkRows, 4};
+    dagrt_tuning tune = {256, kChunkRows, 4, 2};
     // size classes: warp classes then the CTA class, lists concatenated
     int32_t *lists = nullptr;
     int32_t *counters = nullptr;
-    int class_off[kNumWarpClasses + 2] = {0};
+    int class_off[kNumClasses + 1] = {0};
     int max_v = 0, big_vcap = 0, big_ecap = 0, big_grid = 0;
+    int smem_vcap = 0, smem_ecap = 0;  // capacity of the shared-memory CTA class
     unsigned char *gws = nullptr;  // pooled, gws_cap bytes
     int64_t gws_stride = 0;
     size_t gws_cap = 0;
@@ -276,7 +280,9 @@ void dagrt_batch_free(dagrt_batch *b) {
 
 // Size classes for the scheduler: a DAG goes to the smallest warp class whose shared-memory
 // workspace holds its V nodes and E edges, among the classes of at most tune.warp_max_v
-// nodes; the rest go to CTA teams with global workspaces. Each class is ordered by
+// nodes; the rest go to CTA teams -- with a shared-memory workspace while the class's
+// capacity (largest V and E so far, smallest DAGs first) still fits 1/tune.cta_smem of a
+// CTA's shared memory (cta_smem = 0: never), else with global workspaces. Each class is ordered by
 // descending node count (longest work first). Host work plus one list upload.
 static int partition_classes(dagrt_batch *b) {
     dagrt_ctx *ctx = b->ctx;
@@ -285,38 +291,64 @@ static int partition_classes(dagrt_batch *b) {
     int n_warp = 0;  // warp classes enabled
     while (n_warp < kNumWarpClasses && kWarpClassCap[n_warp] <= b->tune.warp_max_v) n_warp++;
     std::vector<int32_t> lists(n_dags);
-    std::vector<std::vector<int32_t>> cls(kNumWarpClasses + 1);
+    std::vector<std::vector<int32_t>> cls(kNumClasses);
     std::vector<int32_t> order(n_dags);
     std::vector<int32_t> cnt(max_v + 2, 0);  // counting sort by descending V
     for (int d = 0; d < n_dags; d++) cnt[max_v - (int)(hn[d + 1] - hn[d])]++;
     for (int i = 1; i < (int)cnt.size(); i++) cnt[i] += cnt[i - 1];
     for (int d = n_dags - 1; d >= 0; d--) order[--cnt[max_v - (int)(hn[d + 1] - hn[d])]] = d;
-    int big_v = 0;
-    int64_t big_e = 0;
+    std::vector<int32_t> big;  // CTA-team DAGs, descending V
     for (int d : order) {
         const int v = (int)(hn[d + 1] - hn[d]);
         const int64_t ed = he[d + 1] - he[d];
         int c = 0;
         while (c < n_warp && (v > kWarpClassCap[c] || ed > (int64_t)kEdgesPerNode * kWarpClassCap[c])) c++;
-        if (c == n_warp) c = kNumWarpClasses;
-        cls[c].push_back(d);
-        if (c == kNumWarpClasses) {
-            big_v = std::max(big_v, v);
-            big_e = std::max(big_e, ed);
+        if (c < n_warp)
+            cls[c].push_back(d);
+        else
+            big.push_back(d);
+    }
+    // cta_smem = k: a workspace takes at most 1/k of the shared memory, so k teams fit per SM
+    const int64_t limit = b->tune.cta_smem > 0 ? sched_smem_limit() / b->tune.cta_smem : 0;
+    int sv = 0, gv = 0;
+    int64_t se = 0, ge = 0;
+    std::vector<char> in_smem(big.size(), 0);
+    for (int i = (int)big.size() - 1; i >= 0; i--) {  // smallest first
+        const int d = big[i];
+        const int v = (int)(hn[d + 1] - hn[d]);
+        const int64_t ed = he[d + 1] - he[d];
+        const int nv = std::max(sv, v);
+        const int64_t ne = std::max(se, ed);
+        if (ne < (1ll << 30) && sched_ws_bytes(nv, (int)ne) <= limit) {
+            sv = nv;
+            se = ne;
+            in_smem[i] = 1;
+        }
+    }
+    for (size_t i = 0; i < big.size(); i++) {
+        const int d = big[i];
+        if (in_smem[i]) {
+            cls[kClsCtaSmem].push_back(d);
+        } else {
+            cls[kClsCtaGlobal].push_back(d);
+            gv = std::max(gv, (int)(hn[d + 1] - hn[d]));
+            ge = std::max(ge, he[d + 1] - he[d]);
         }
     }
     int off = 0;
-    for (int c = 0; c <= kNumWarpClasses; c++) {
+    for (int c = 0; c < kNumClasses; c++) {
         b->class_off[c] = off;
         std::copy(cls[c].begin(), cls[c].end(), lists.begin() + off);
         off += (int)cls[c].size();
     }
-    b->class_off[kNumWarpClasses + 1] = off;
-    b->big_vcap = big_v;
-    b->big_ecap = (int)big_e;
+    b->class_off[kNumClasses] = off;
+    b->smem_vcap = sv;
+    b->smem_ecap = (int)se;
+    b->big_vcap = gv;
+    b->big_ecap = (int)ge;
     if (n_dags > 0)
         CK(cudaMemcpyAsync(b->lists, lists.data(), 4 * n_dags, cudaMemcpyHostToDevice, ctx->stream), "copy class lists");
-    const int n_big = b->class_off[kNumWarpClasses + 1] - b->class_off[kNumWarpClasses];
+    const int n_big = b->class_off[kClsCtaGlobal + 1] - b->class_off[kClsCtaGlobal];
     if (n_big > 0) {
         b->big_grid = std::min(sched_cta_grid(ctx->n_sm), n_big);
         b->gws_stride = sched_ws_bytes(b->big_vcap, b->big_ecap);
@@ -605,7 +637,7 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
         // size classes run concurrently: fork from the context stream, join back into it
         CK(cudaEventRecord(ctx->fork, ctx->stream), "record fork");
         int used[dagrt_ctx::kSide], nused = 0;
-        for (int c = 0; c <= kNumWarpClasses; c++) {
+        for (int c = 0; c < kNumClasses; c++) {
             const int n = b->class_off[c + 1] - b->class_off[c];
             if (n == 0) continue;
             cudaStream_t st = ctx->side[c];
@@ -615,6 +647,10 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
             a.counter = b->counters + c;
             if (c < kNumWarpClasses) {
                 CK(sched_launch_warp(kWarpClassCap[c], a, ctx->n_sm, st), "launch scheduler (warp teams)");
+            } else if (c == kClsCtaSmem) {
+                a.vcap = b->smem_vcap;
+                a.ecap = b->smem_ecap;
+                CK(sched_launch_cta_smem(a, ctx->n_sm, st), "launch scheduler (CTA teams, shared memory)");
             } else {
                 a.gws = b->gws;
                 a.gws_stride = b->gws_stride;
@@ -1199,7 +1235,9 @@ extern "C" int dagrt_set_tuning(dagrt_batch *b, const dagrt_tuning *t) {
     if (t->item_warps < 1 || t->item_warps > 8)
         return fail(ctx, DAGRT_E_INVAL, "dagrt_set_tuning: item_warps must be in [1, 8]");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const bool repart = t->warp_max_v != b->tune.warp_max_v;
+    if (t->cta_smem < 0 || t->cta_smem > 4)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_set_tuning: cta_smem must be in [0, 4]");
+    const bool repart = t->warp_max_v != b->tune.warp_max_v || t->cta_smem != b->tune.cta_smem;
     b->tune = *t;
     if (repart) {
         CK(cudaStreamSynchronize(ctx->stream), "synchronize");  // the lists may be in use
@@ -1247,9 +1285,10 @@ extern "C" int dagrt_autotune_schedule(dagrt_batch *b, int32_t variant, int32_t 
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     dagrt_tuning best = b->tune;
     float bt = -1.f;
-    for (int w : {64, 128, 192, 256}) {
+    for (int cfg = 0; cfg < 20; cfg++) {
         dagrt_tuning t = b->tune;
-        t.warp_max_v = w;
+        t.warp_max_v = 64 * (1 + cfg % 4);
+        t.cta_smem = cfg / 4;
         int rc = dagrt_set_tuning(b, &t);
         if (rc) return rc;
         dagrt_schedule_out o;

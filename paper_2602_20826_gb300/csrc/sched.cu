@@ -931,12 +931,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_sched_warp(SchedArgs a) {
     }
 }
 
-template <int NT>
+// CTA teams for large DAGs: the workspace sized for (a.vcap, a.ecap) lives in dynamic shared
+// memory (SMEM) or in the global block a.gws + blockIdx.x * a.gws_stride.
+template <int NT, bool SMEM>
 __global__ void __launch_bounds__(NT) k_sched_cta(SchedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t red[NT / 32];
     __shared__ int idx_s;
     Ws ws;
-    ws_carve(a.gws + (int64_t)blockIdx.x * a.gws_stride, a.vcap, a.ecap, &ws);
+    ws_carve(SMEM ? smem : a.gws + (int64_t)blockIdx.x * a.gws_stride, a.vcap, a.ecap, &ws);
     Team<NT> tm{(int)threadIdx.x, red};
     for (;;) {
         if (threadIdx.x == 0) idx_s = atomicAdd(a.counter, 1);
@@ -980,7 +983,7 @@ cudaError_t sched_launch_warp(int vc, const SchedArgs &a, int n_sm, cudaStream_t
 
 int sched_cta_grid(int n_sm) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_cta<kCtaThreads>, kCtaThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_cta<kCtaThreads, false>, kCtaThreads, 0) !=
             cudaSuccess || per_sm < 1)
         per_sm = 1;
     return n_sm * per_sm;
@@ -988,7 +991,31 @@ int sched_cta_grid(int n_sm) {
 
 cudaError_t sched_launch_cta(const SchedArgs &a, int grid, cudaStream_t st) {
     if (grid < 1 || a.n_list < 1) return cudaSuccess;
-    k_sched_cta<kCtaThreads><<<grid, kCtaThreads, 0, st>>>(a);
+    k_sched_cta<kCtaThreads, false><<<grid, kCtaThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int64_t sched_smem_limit() {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    return optin - (int64_t)sizeof(uint64_t) * (kCtaThreads / 32) - 64;  // the kernel's static shared memory
+}
+
+cudaError_t sched_launch_cta_smem(const SchedArgs &a, int n_sm, cudaStream_t st) {
+    if (a.n_list < 1) return cudaSuccess;
+    const int64_t bytes = sched_ws_bytes(a.vcap, a.ecap);
+    cudaError_t e = cudaFuncSetAttribute(k_sched_cta<kCtaThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_cta<kCtaThreads, true>, kCtaThreads, bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = n_sm * per_sm;
+    if (grid > a.n_list) grid = a.n_list;
+    k_sched_cta<kCtaThreads, true><<<grid, kCtaThreads, bytes, st>>>(a);
     return cudaGetLastError();
 }
 

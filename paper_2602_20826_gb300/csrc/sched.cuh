@@ -48,5 +48,9 @@ int64_t sched_ws_bytes(int vc, int ec);
 cudaError_t sched_launch_warp(int vc, const SchedArgs &a, int n_sm, cudaStream_t st);
 int sched_cta_grid(int n_sm);
 cudaError_t sched_launch_cta(const SchedArgs &a, int grid, cudaStream_t st);
+// CTA teams with the workspace (a.vcap, a.ecap) in shared memory: sched_ws_bytes of the
+// class must not exceed sched_smem_limit()
+int64_t sched_smem_limit();
+cudaError_t sched_launch_cta_smem(const SchedArgs &a, int n_sm, cudaStream_t st);
 
 }  // namespace dagrt

@@ -79,7 +79,8 @@ dagrt_propose = _sig("dagrt_propose", C.c_int, [_vp, _vp, C.c_int32, _vp, _vp, _
 
 
 class dagrt_tuning(C.Structure):
-    _fields_ = [("warp_max_v", C.c_int32), ("chunk_rows", C.c_int32), ("item_warps", C.c_int32)]
+    _fields_ = [("warp_max_v", C.c_int32), ("chunk_rows", C.c_int32), ("item_warps", C.c_int32),
+                ("cta_smem", C.c_int32)]
 
 
 dagrt_get_tuning = _sig("dagrt_get_tuning", C.c_int, [_vp, C.POINTER(dagrt_tuning)])
@@ -93,6 +94,11 @@ dagrt_graph_begin = _sig("dagrt_graph_begin", C.c_int, [_vp])
 dagrt_graph_end = _sig("dagrt_graph_end", C.c_int, [_vp, C.POINTER(_vp)])
 dagrt_graph_launch = _sig("dagrt_graph_launch", C.c_int, [_vp])
 dagrt_graph_free = _sig("dagrt_graph_free", None, [_vp])
+
+
+def _tdict(t):
+    return {"warp_max_v": t.warp_max_v, "chunk_rows": t.chunk_rows, "item_warps": t.item_warps,
+            "cta_smem": t.cta_smem}
 
 
 class DagrtError(RuntimeError):
@@ -230,18 +236,19 @@ class LoadedBatch:
     def tuning(self) -> dict:
         t = dagrt_tuning()
         self.ctx.check(dagrt_get_tuning(self.h, C.byref(t)))
-        return {"warp_max_v": t.warp_max_v, "chunk_rows": t.chunk_rows, "item_warps": t.item_warps}
+        return _tdict(t)
 
     def set_tuning(self, **kw):
         cur = self.tuning()
         cur.update(kw)
-        t = dagrt_tuning(int(cur["warp_max_v"]), int(cur["chunk_rows"]), int(cur["item_warps"]))
+        t = dagrt_tuning(int(cur["warp_max_v"]), int(cur["chunk_rows"]), int(cur["item_warps"]),
+                         int(cur["cta_smem"]))
         self.ctx.check(dagrt_set_tuning(self.h, C.byref(t)))
 
     def autotune_schedule(self, variant: int = VAR_PAPER, reps: int = 3):
         t, ms = dagrt_tuning(), C.c_float(0)
         self.ctx.check(dagrt_autotune_schedule(self.h, int(variant), int(reps), C.byref(t), C.byref(ms)))
-        return {"warp_max_v": t.warp_max_v, "chunk_rows": t.chunk_rows, "item_warps": t.item_warps}, ms.value
+        return _tdict(t), ms.value
 
     def autotune_bound(self, variant_ids, n_alloc: int, m_alloc, cand_stride: int, reps: int = 3):
         """m_alloc: a torch CUDA tensor (device candidates)."""
@@ -249,7 +256,7 @@ class LoadedBatch:
         t, ms = dagrt_tuning(), C.c_float(0)
         self.ctx.check(dagrt_autotune_bound(self.h, len(variant_ids), vids, int(n_alloc), _ptr(m_alloc),
                                             int(cand_stride), int(reps), C.byref(t), C.byref(ms)))
-        return {"warp_max_v": t.warp_max_v, "chunk_rows": t.chunk_rows, "item_warps": t.item_warps}, ms.value
+        return _tdict(t), ms.value
 
     def schedule(self, variant: int = VAR_PAPER, fields=("bound", "status"), extra_cap=None,
                  out=None, check: bool = True):

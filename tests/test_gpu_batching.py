@@ -33,9 +33,9 @@ def test_schedule_identical_for_every_warp_cutoff(ctx):
     b = _mixed_batch()
     lb = ctx.load(b)
     ref = None
-    for w in (256, 0, 64, 128, 192):
-        lb.set_tuning(warp_max_v=w)
-        assert lb.tuning()["warp_max_v"] == w
+    for w, cs in ((256, 1), (256, 0), (0, 1), (0, 0), (64, 2), (128, 3), (192, 4)):
+        lb.set_tuning(warp_max_v=w, cta_smem=cs)
+        assert lb.tuning()["warp_max_v"] == w and lb.tuning()["cta_smem"] == cs
         res = lb.schedule(0, fields=FIELDS, check=False)
         if ref is None:
             ref = res
@@ -71,7 +71,8 @@ def test_bound_identical_for_every_chunking(ctx):
 def test_tuning_rejects_bad_values(ctx):
     from paper_2602_20826_gb300.dagrt import DagrtError, E_INVAL
     lb = ctx.load(wl.small_config(2, 3, 5, 20, seed=1))
-    for kw in ({"warp_max_v": 100}, {"chunk_rows": 4}, {"chunk_rows": 300}, {"item_warps": 0}, {"item_warps": 9}):
+    for kw in ({"warp_max_v": 100}, {"chunk_rows": 4}, {"chunk_rows": 300}, {"item_warps": 0}, {"item_warps": 9},
+               {"cta_smem": 5}, {"cta_smem": -1}):
         with pytest.raises(DagrtError) as e:
             lb.set_tuning(**kw)
         assert e.value.code == E_INVAL
