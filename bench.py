@@ -49,6 +49,8 @@ def _args():
                         "cfg4-learned: learned proposal + exact check vs plain search")
     p.add_argument("--train-dags", type=int, default=50000, help="cfg4-learned: training DAGs")
     p.add_argument("--epochs", type=int, default=8, help="cfg4-learned: training epochs")
+    p.add_argument("--eval-dags", type=int, default=10000,
+                   help="cfg4-learned: evaluation DAGs (smaller cases for profiling)")
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="bounded CPU work of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -207,7 +209,7 @@ def run_cfg4_learned(args):
     for lb, _ in data:
         lb.free()
     del data
-    be = wl.config(4)
+    be = wl.config(4, n_dags=args.eval_dags)
     keys = ("node_off", "edge_off", "row_ptr", "col", "wcet", "k64")
     dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(be, k))).cuda() for k in keys}
     clocks = ClockSampler(torch.cuda.current_device())

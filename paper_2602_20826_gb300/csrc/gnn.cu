@@ -183,12 +183,87 @@ __device__ __forceinline__ uint2 pack4(const float *f) {
 }
 
 // ------------------------------------------------------------------ forward layer
-// Persistent CTAs of 128 threads over 128-row tiles: gather the A tile (K = 3 KIN) into
-// shared memory, one tcgen05 MMA chain against W^T (resident), epilogue bias + ReLU -> bf16.
+// Persistent CTAs of kFwdWarps warps over 128-row tiles. The A tile (K = 3 KIN) is gathered
+// straight into shared memory: a group of KIN/8 lanes owns one row (16 bytes = 8 features
+// per lane), so a warp gathers 32 / (KIN/8) rows at once, and the neighbour loops are
+// unrolled by 4 so that several neighbour rows are in flight per lane (the gather is
+// latency-bound: neighbours are scattered over the DAG). One thread then issues the
+// tcgen05 MMA chain against the resident W^T; the epilogue (bias, ReLU, bf16) reads TMEM with
+// the first 16 warps: warp w takes TMEM lanes 32 (w % 4) .. + 31 and columns 32 (w / 4) .. + 31.
+constexpr int kFwdWarps = 32;
+
+__device__ __forceinline__ void acc8(float *a, uint4 u) {
+    a[0] += bf2f(u.x & 0xffff);
+    a[1] += bf2f(u.x >> 16);
+    a[2] += bf2f(u.y & 0xffff);
+    a[3] += bf2f(u.y >> 16);
+    a[4] += bf2f(u.z & 0xffff);
+    a[5] += bf2f(u.z >> 16);
+    a[6] += bf2f(u.w & 0xffff);
+    a[7] += bf2f(u.w >> 16);
+}
+
+// mean over the rows idx[b .. e) of h, features [8 sub, 8 sub + 8)
 template <int KIN>
-__global__ void __launch_bounds__(128) k_gnn_fwd(GnnGraph g, const uint16_t *__restrict__ h_in,
-                                                 const uint16_t *__restrict__ wt, const float *__restrict__ bias,
-                                                 uint16_t *__restrict__ h_out, int32_t *err) {
+__device__ __forceinline__ void mean_rows(const uint16_t *__restrict__ h, const int32_t *__restrict__ idx, int b,
+                                          int e, int sub, float *m) {
+#pragma unroll
+    for (int q = 0; q < 8; q++) m[q] = 0.f;
+    int i = b;
+    for (; i + 4 <= e; i += 4) {
+        const int32_t j0 = __ldg(idx + i), j1 = __ldg(idx + i + 1), j2 = __ldg(idx + i + 2), j3 = __ldg(idx + i + 3);
+        const uint4 u0 = __ldg((const uint4 *)(h + (int64_t)j0 * KIN) + sub);
+        const uint4 u1 = __ldg((const uint4 *)(h + (int64_t)j1 * KIN) + sub);
+        const uint4 u2 = __ldg((const uint4 *)(h + (int64_t)j2 * KIN) + sub);
+        const uint4 u3 = __ldg((const uint4 *)(h + (int64_t)j3 * KIN) + sub);
+        acc8(m, u0);
+        acc8(m, u1);
+        acc8(m, u2);
+        acc8(m, u3);
+    }
+    for (; i < e; i++) acc8(m, __ldg((const uint4 *)(h + (int64_t)__ldg(idx + i) * KIN) + sub));
+    const float inv = e > b ? 1.f / (float)(e - b) : 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; q++) m[q] *= inv;
+}
+
+__device__ __forceinline__ uint4 pack8(const float *f) {
+    return make_uint4((uint32_t)f2bf(f[0]) | ((uint32_t)f2bf(f[1]) << 16), (uint32_t)f2bf(f[2]) | ((uint32_t)f2bf(f[3]) << 16),
+                      (uint32_t)f2bf(f[4]) | ((uint32_t)f2bf(f[5]) << 16), (uint32_t)f2bf(f[6]) | ((uint32_t)f2bf(f[7]) << 16));
+}
+
+// rows [32 w / ... ) of the tile: the A operand [h | mean_pred h | mean_succ h] in K-major order
+template <int KIN>
+__device__ __forceinline__ void gather_tile(const GnnGraph &g, const uint16_t *__restrict__ h_in, int64_t tile,
+                                            unsigned char *sA, int w, int lane) {
+    constexpr int K = 3 * KIN, LPR = KIN / 8, RPW = 32 / LPR;  // lanes per row, rows per warp pass
+    constexpr int ROWS = 128 / kFwdWarps;                      // rows of the tile per warp
+    const int sub = lane % LPR;
+    for (int r0 = 0; r0 < ROWS; r0 += RPW) {
+        const int rl = r0 + lane / LPR;
+        if (rl >= ROWS) continue;
+        const int r = w * ROWS + rl;
+        const int64_t v = tile * 128 + r;
+        uint4 s0 = make_uint4(0, 0, 0, 0), s1 = s0, s2 = s0;
+        if (v < g.n_nodes) {
+            s0 = __ldg((const uint4 *)(h_in + v * KIN) + sub);
+            float m[8];
+            mean_rows<KIN>(h_in, g.pred_idx, g.pred_off[v], g.pred_off[v + 1], sub, m);
+            s1 = pack8(m);
+            mean_rows<KIN>(h_in, g.succ_idx, g.succ_off[v], g.succ_off[v + 1], sub, m);
+            s2 = pack8(m);
+        }
+        *(uint4 *)(sA + kmajor_off(r, 8 * sub, K)) = s0;
+        *(uint4 *)(sA + kmajor_off(r, KIN + 8 * sub, K)) = s1;
+        *(uint4 *)(sA + kmajor_off(r, 2 * KIN + 8 * sub, K)) = s2;
+    }
+}
+
+template <int KIN>
+__global__ void __launch_bounds__(32 * kFwdWarps) k_gnn_fwd(GnnGraph g, const uint16_t *__restrict__ h_in,
+                                                            const uint16_t *__restrict__ wt,
+                                                            const float *__restrict__ bias,
+                                                            uint16_t *__restrict__ h_out, int32_t *err) {
     constexpr int K = 3 * KIN;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
@@ -196,7 +271,7 @@ __global__ void __launch_bounds__(128) k_gnn_fwd(GnnGraph g, const uint16_t *__r
     __shared__ float sbias[kHidden];
     unsigned char *sA = sm, *sB = sm + 128 * K * 2;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    for (int i = t; i < kHidden * (K / 8); i += 128) {  // W^T [H x K] -> K-major B operand
+    for (int i = t; i < kHidden * (K / 8); i += blockDim.x) {  // W^T [H x K] -> K-major B operand
         const int r = i / (K / 8), kc = (i % (K / 8)) * 8;
         *(uint4 *)(sB + kmajor_off(r, kc, K)) = *(const uint4 *)(wt + (size_t)r * K + kc);
     }
@@ -208,19 +283,11 @@ __global__ void __launch_bounds__(128) k_gnn_fwd(GnnGraph g, const uint16_t *__r
     tmem_fence_after();
     const uint32_t taddr = tslot;
     const int64_t n_tiles = (g.n_nodes + 127) / 128;
+    const int lq = w & 3, cb = w >> 2;  // epilogue: TMEM lane quarter and 32-column block
     uint32_t phase = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        for (int rr = 0; rr < 32; rr++) {  // warp w gathers rows 32w .. 32w+31
-            const int r = 32 * w + rr;
-            float f0[4], f1[4], f2[4];
-            gather_row<KIN>(g, h_in, tile * 128 + r, lane, f0, f1, f2);
-            if (lane * 4 < KIN) {
-                *(uint2 *)(sA + kmajor_off(r, 4 * lane, K)) = pack4(f0);
-                *(uint2 *)(sA + kmajor_off(r, KIN + 4 * lane, K)) = pack4(f1);
-                *(uint2 *)(sA + kmajor_off(r, 2 * KIN + 4 * lane, K)) = pack4(f2);
-            }
-        }
+        gather_tile<KIN>(g, h_in, tile, sA, w, lane);
         fence_async_smem();
         __syncthreads();
         if (t == 0) {
@@ -231,25 +298,24 @@ __global__ void __launch_bounds__(128) k_gnn_fwd(GnnGraph g, const uint16_t *__r
         ok = __syncthreads_and(mbar_wait_parity(&bar, phase, kWaitLimit)) != 0;  // uniform across the CTA
         phase ^= 1;
         tmem_fence_after();
-        if (ok) {
-            const int64_t v = tile * 128 + t;  // this thread's TMEM lane = row t
-            for (int c0 = 0; c0 < kHidden; c0 += 32) {
-                float acc[32];
-                tmem_ld32(taddr + ((uint32_t)(32 * w) << 16) + c0, acc);
-                if (v < g.n_nodes) {
-                    uint32_t pk[16];
+        if (ok && w < 16) {
+            const int64_t v = tile * 128 + 32 * lq + lane;  // this thread's TMEM lane = row 32 lq + lane
+            const int c0 = 32 * cb;
+            float acc[32];
+            tmem_ld32(taddr + ((uint32_t)(32 * lq) << 16) + c0, acc);
+            if (v < g.n_nodes) {
+                uint32_t pk[16];
 #pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const float a0 = fmaxf(acc[2 * i] + sbias[c0 + 2 * i], 0.f);
-                        const float a1 = fmaxf(acc[2 * i + 1] + sbias[c0 + 2 * i + 1], 0.f);
-                        pk[i] = (uint32_t)f2bf(a0) | ((uint32_t)f2bf(a1) << 16);
-                    }
-                    uint4 *dst = (uint4 *)(h_out + v * kHidden + c0);
-#pragma unroll
-                    for (int i = 0; i < 4; i++) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                for (int i = 0; i < 16; i++) {
+                    const float a0 = fmaxf(acc[2 * i] + sbias[c0 + 2 * i], 0.f);
+                    const float a1 = fmaxf(acc[2 * i + 1] + sbias[c0 + 2 * i + 1], 0.f);
+                    pk[i] = (uint32_t)f2bf(a0) | ((uint32_t)f2bf(a1) << 16);
                 }
+                uint4 *dst = (uint4 *)(h_out + v * kHidden + c0);
+#pragma unroll
+                for (int i = 0; i < 4; i++) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
             }
-        } else if (t == 0 && err) {
+        } else if (!ok && t == 0 && err) {
             atomicExch(err, DAGRT_E_TIMEOUT);
         }
         tmem_fence_before();
@@ -265,10 +331,15 @@ static cudaError_t launch_fwd(GnnGraph g, const uint16_t *h_in, const uint16_t *
     const int smem = 2 * 128 * K * 2;
     cudaError_t e = cudaFuncSetAttribute(k_gnn_fwd<KIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gnn_fwd<KIN>, 32 * kFwdWarps, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 4) per_sm = 4;  // 4 x 128 TMEM columns per SM
     const int64_t n_tiles = (g.n_nodes + 127) / 128;
-    int grid = (int)(n_tiles < n_sm ? n_tiles : n_sm);
+    int grid = (int)(n_tiles < (int64_t)n_sm * per_sm ? n_tiles : (int64_t)n_sm * per_sm);
     if (grid < 1) return cudaSuccess;
-    k_gnn_fwd<KIN><<<grid, 128, smem, st>>>(g, h_in, wt, bias, h_out, err);
+    k_gnn_fwd<KIN><<<grid, 32 * kFwdWarps, smem, st>>>(g, h_in, wt, bias, h_out, err);
     return cudaGetLastError();
 }
 
