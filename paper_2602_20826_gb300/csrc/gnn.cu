@@ -23,8 +23,8 @@ __device__ __forceinline__ uint16_t f2bf(float f) {
 }
 
 // ------------------------------------------------------------------ graph
-// One warp per DAG: global successor CSR, in-degrees, then predecessor lists filled by one
-// lane in edge order (so every list is in increasing predecessor id: deterministic).
+// One warp per DAG: global successor CSR, in-degrees, then predecessor lists filled by all
+// lanes and sorted per node (every list in increasing predecessor id: deterministic).
 __global__ void k_gnn_graph(int32_t n_dags, const int64_t *node_off, const int64_t *edge_off,
                             const int32_t *row_ptr, const int32_t *col, int32_t *pred_off, int32_t *pred_idx,
                             int32_t *succ_off, int32_t *succ_idx, int32_t *cursor) {
@@ -58,17 +58,30 @@ __global__ void k_gnn_graph(int32_t n_dags, const int64_t *node_off, const int64
             carry += __shfl_sync(FULL, x, 31);
         }
         __syncwarp();
-        if (lane == 0) {
-            if (d == n_dags - 1) {
-                pred_off[node_off[n_dags]] = (int32_t)edge_off[n_dags];
-                succ_off[node_off[n_dags]] = (int32_t)edge_off[n_dags];
+        if (lane == 0 && d == n_dags - 1) {
+            pred_off[node_off[n_dags]] = (int32_t)edge_off[n_dags];
+            succ_off[node_off[n_dags]] = (int32_t)edge_off[n_dags];
+        }
+        for (int v = lane; v < V; v += 32) cursor[n0 + v] = 0;
+        __syncwarp();
+        for (int u = lane; u < V; u += 32)  // fill in any order ...
+            for (int e = rp[u]; e < rp[u + 1]; e++) {
+                const int s = cl[e];
+                pred_idx[pred_off[n0 + s] + atomicAdd(&cursor[n0 + s], 1)] = (int32_t)(n0 + u);
             }
-            for (int v = 0; v < V; v++) cursor[n0 + v] = 0;
-            for (int u = 0; u < V; u++)
-                for (int e = rp[u]; e < rp[u + 1]; e++) {
-                    const int s = cl[e];
-                    pred_idx[pred_off[n0 + s] + cursor[n0 + s]++] = (int32_t)(n0 + u);
+        __syncwarp();
+        for (int v = lane; v < V; v += 32) {  // ... then sort each list (increasing predecessor id)
+            int32_t *p = pred_idx + pred_off[n0 + v];
+            const int n = cursor[n0 + v];
+            for (int i = 1; i < n; i++) {
+                const int32_t x = p[i];
+                int j = i - 1;
+                while (j >= 0 && p[j] > x) {
+                    p[j + 1] = p[j];
+                    j--;
                 }
+                p[j + 1] = x;
+            }
         }
         __syncwarp();
     }
