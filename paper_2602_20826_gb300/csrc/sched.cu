@@ -278,93 +278,126 @@ __device__ void extra_edges(const Ws &ws, const SchedArgs &a, const Dag &g, int 
     acc.nextra += (int64_t)nl * outdeg + (int64_t)(acc.nrel - np - nwhole);
 }
 
-// Group j scheduled by one thread (groups with few members).
-__device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int j, Acc &acc) {
-    const uint32_t M = g.M;
-    const int gb = ws.gstart[j], ge = ws.gstart[j + 1];
-    int np = 0;
-    uint64_t Wg = 0;
-    for (int i = gb; i < ge; i++) {
-        const int v = ws.gmem[i];
-        if (!(ws.st[v] & ST_DONE)) {
-            np++;
-            Wg += ws.rem[v];
-        }
-    }
-    if (np == 0) {  // every member already ran as a parallel node: the group is dropped
-        if (a.o.group_R) a.o.group_R[g.n0 + j] = 0;
-        return;
-    }
-    // Eq.5; a single member gets round(C^ M / C^) = M, i.e. m = min(C^, M)
-    uint32_t sum_m = 0;
-    for (int i = gb; i < ge; i++) {
-        const int v = ws.gmem[i];
-        if (ws.st[v] & ST_DONE) continue;
-        const uint32_t x = ws.rem[v];
-        uint32_t m;
-        if (np == 1) {
-            m = x < M ? x : M;
-        } else {
-            const uint64_t num = 2ull * x * M + Wg, den = 2ull * Wg;
-            uint64_t r = (num >> 32) == 0 && (den >> 32) == 0 ? (uint64_t)((uint32_t)num / (uint32_t)den) : num / den;
-            if (r < 1) r = 1;
-            m = (uint32_t)(r < x ? r : x);
-        }
-        ws.mm[v] = (uint16_t)m;
-        sum_m += m;
-    }
-    while (sum_m > M) {  // keep sum m_i <= M: trim the largest m (ties: higher id)
-        int best = -1;
-        for (int i = gb; i < ge; i++) {
-            const int v = ws.gmem[i];
-            if (ws.st[v] & ST_DONE) continue;
-            if (best < 0 || ws.mm[v] >= ws.mm[best]) best = v;
-        }
-        ws.mm[best]--;
-        sum_m--;
-    }
-    // Eq.1 per member and Lemma 1: R(pi_j) = max C_i, v_R = lowest id with C_i = R; rows
+// Group j with few members: lane 0 of the team's first warp runs Eq.5, Lemma 1, the
+// parallel launches and the extra edges serially; the 32 lanes then release the finished
+// nodes' successors together (the decrements commute). `acc` is valid in lane 0 only.
+__device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int j, Acc &acc, int lane) {
+    int nf = 0;
     uint64_t R = 0;
-    int vR = -1;
-    for (int i = gb; i < ge; i++) {
-        const int v = ws.gmem[i];
-        if (ws.st[v] & ST_DONE) continue;
-        const uint32_t x = ws.rem[v], m = ws.mm[v];
-        const uint64_t c = (x == ws.load[v] && m == (x < M ? x : M)) ? ws.cfull[v] : exec_time(x, ws.kk[v], m, M);
-        if (c > R) {
-            R = c;
-            vR = v;
-        }
-        write_row(a, g, acc.nrows++, v, v, j, x, ws.kk[v], m, c);
-    }
-    int nl, nwhole;
-    launch_parallel(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
-    extra_edges(ws, a, g, j, vR, np, nl, nwhole, acc);
-    // members and whole launches finish with pi_j and release their successors
-    for (int i = gb; i < ge + nl; i++) {
-        int v;
-        if (i < ge) {
-            v = ws.gmem[i];
-            if (ws.st[v] & ST_DONE) continue;
+    if (lane == 0) {
+        const uint32_t M = g.M;
+        const int gb = ws.gstart[j], ge = ws.gstart[j + 1];
+        int np = 0, vR = -1;
+        uint32_t sum_m = 0;
+        if (ge - gb == 1) {  // one member: Eq.5 gives m = min(C^, M)
+            const int v = ws.gmem[gb];
+            if (!(ws.st[v] & ST_DONE)) {
+                np = 1;
+                const uint32_t x = ws.rem[v], m = x < M ? x : M;
+                ws.mm[v] = (uint16_t)m;
+                sum_m = m;
+                const uint64_t c = x == ws.load[v] ? ws.cfull[v] : exec_time(x, ws.kk[v], m, M);
+                R = c;
+                vR = v;
+                write_row(a, g, acc.nrows++, v, v, j, x, ws.kk[v], m, c);
+            }
         } else {
-            v = ws.lst[i - ge];
-            if (v >= g.V) continue;  // a segment: its node is not finished
+            uint64_t Wg = 0;
+            for (int i = gb; i < ge; i++) {
+                const int v = ws.gmem[i];
+                if (!(ws.st[v] & ST_DONE)) {
+                    np++;
+                    Wg += ws.rem[v];
+                }
+            }
+            if (np > 0) {
+                // Eq.5; a single member gets round(C^ M / C^) = M, i.e. m = min(C^, M)
+                for (int i = gb; i < ge; i++) {
+                    const int v = ws.gmem[i];
+                    if (ws.st[v] & ST_DONE) continue;
+                    const uint32_t x = ws.rem[v];
+                    uint32_t m;
+                    if (np == 1) {
+                        m = x < M ? x : M;
+                    } else {
+                        const uint64_t num = 2ull * x * M + Wg, den = 2ull * Wg;
+                        uint64_t r = (num >> 32) == 0 && (den >> 32) == 0 ? (uint64_t)((uint32_t)num / (uint32_t)den)
+                                                                          : num / den;
+                        if (r < 1) r = 1;
+                        m = (uint32_t)(r < x ? r : x);
+                    }
+                    ws.mm[v] = (uint16_t)m;
+                    sum_m += m;
+                }
+                while (sum_m > M) {  // keep sum m_i <= M: trim the largest m (ties: higher id)
+                    int best = -1;
+                    for (int i = gb; i < ge; i++) {
+                        const int v = ws.gmem[i];
+                        if (ws.st[v] & ST_DONE) continue;
+                        if (best < 0 || ws.mm[v] >= ws.mm[best]) best = v;
+                    }
+                    ws.mm[best]--;
+                    sum_m--;
+                }
+                // Eq.1 per member and Lemma 1: R(pi_j) = max C_i, v_R = lowest id with C_i = R
+                for (int i = gb; i < ge; i++) {
+                    const int v = ws.gmem[i];
+                    if (ws.st[v] & ST_DONE) continue;
+                    const uint32_t x = ws.rem[v], m = ws.mm[v];
+                    const uint64_t c =
+                        (x == ws.load[v] && m == (x < M ? x : M)) ? ws.cfull[v] : exec_time(x, ws.kk[v], m, M);
+                    if (c > R) {
+                        R = c;
+                        vR = v;
+                    }
+                    write_row(a, g, acc.nrows++, v, v, j, x, ws.kk[v], m, c);
+                }
+            }
         }
-        ws.st[v] = ST_DONE;
-        ws.rem[v] = 0;
-        if (a.o.exec_group) a.o.exec_group[g.n0 + v] = j;
-        ws.relmask[ws.rank[v] >> 6] &= ~(1ull << (ws.rank[v] & 63));
-        acc.nrel--;
-        for (int e = g.rp[v]; e < g.rp[v + 1]; e++) {
+        if (np == 0) {  // every member already ran as a parallel node: the group is dropped
+            if (a.o.group_R) a.o.group_R[g.n0 + j] = 0;
+        } else {
+            int nl, nwhole;
+            launch_parallel(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
+            extra_edges(ws, a, g, j, vR, np, nl, nwhole, acc);
+            // members and whole launches finish with pi_j
+            for (int i = gb; i < ge + nl; i++) {
+                int v;
+                if (i < ge) {
+                    v = ws.gmem[i];
+                    if (ws.st[v] & ST_DONE) continue;
+                } else {
+                    v = ws.lst[i - ge];
+                    if (v >= g.V) continue;  // a segment: its node is not finished
+                }
+                ws.st[v] = ST_DONE;
+                ws.rem[v] = 0;
+                if (a.o.exec_group) a.o.exec_group[g.n0 + v] = j;
+                ws.relmask[ws.rank[v] >> 6] &= ~(1ull << (ws.rank[v] & 63));
+                ws.tmp[nf++] = v;
+            }
+            acc.nrel -= nf;
+            if (a.o.group_R) a.o.group_R[g.n0 + j] = (int64_t)R;
+            acc.bound += R;
+        }
+    }
+    nf = __shfl_sync(FULL, nf, 0);
+    __syncwarp();
+    // ... and release their successors
+    int released = 0;
+    for (int f = 0; f < nf; f++) {
+        const int v = ws.tmp[f];
+        for (int e = g.rp[v] + lane; e < g.rp[v + 1]; e += 32) {
             const int s = g.col[e];
-            if (--ws.cnt[s] == 0) {
-                ws.relmask[ws.rank[s] >> 6] |= 1ull << (ws.rank[s] & 63);
-                acc.nrel++;
+            if (atomicSub(&ws.cnt[s], 1) == 1) {
+                atomicOr((unsigned long long *)&ws.relmask[ws.rank[s] >> 6], 1ull << (ws.rank[s] & 63));
+                released++;
             }
         }
     }
-    if (a.o.group_R) a.o.group_R[g.n0 + j] = (int64_t)R;
-    acc.bound += R;
+    released = __reduce_add_sync(FULL, released);
+    if (lane == 0) acc.nrel += released;
+    __syncwarp();
 }
 
 // Group j scheduled by the whole team (groups with many members). `acc` is only valid in
@@ -873,8 +906,8 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     for (int j = 0; j < G;) {
         int j1 = j;
         while (j1 < G && ws.gstart[j1 + 1] - ws.gstart[j1] <= kSerialMax) j1++;
-        if (lead)
-            for (int q = j; q < j1; q++) group_serial(ws, a, g, q, acc);
+        if (tm.t < 32)  // the team's first warp
+            for (int q = j; q < j1; q++) group_serial(ws, a, g, q, acc, tm.t);
         if (j1 < G) {
             if (lead) sc[8] = acc.nrows;
             tm.sync();
