@@ -141,6 +141,8 @@ struct Acc {
     int64_t nextra;
     int nrows, nseg, nrel;  // plan rows, segments, released-and-unfinished nodes
     bool err;
+    int lastr;       // the last plan row written by this thread (-1: unknown) ...
+    uint32_t lastz;  // ... and its packed m | k << 16, to mark it as the group's last row
 };
 
 __device__ inline void write_failure(const SchedArgs &a, int d, int code) {
@@ -157,15 +159,17 @@ __device__ inline void write_failure(const SchedArgs &a, int d, int code) {
 
 // plan row r: `id` is the node (< V) or segment (>= V) it runs, `owner` the node whose
 // allocation it uses (the segment's parent for a segment)
-__device__ inline void write_row(const SchedArgs &a, const Dag &g, int r, int id, int owner, int group,
-                                 uint32_t load, uint32_t k, uint32_t m, uint64_t c) {
-    if (r >= 2 * g.V) return;
+__device__ inline uint32_t write_row(const SchedArgs &a, const Dag &g, int r, int id, int owner, int group,
+                                     uint32_t load, uint32_t k, uint32_t m, uint64_t c) {
+    const uint32_t z = m | (k << 16);
+    if (r >= 2 * g.V) return z;
     const int64_t i = g.rbase + r;
-    if (a.plan) a.plan[i] = make_uint4(load, (uint32_t)c, m | (k << 16), (uint32_t)owner);
+    if (a.plan) a.plan[i] = make_uint4(load, (uint32_t)c, z, (uint32_t)owner);
     if (a.o.row_id) a.o.row_id[i] = id;
     if (a.o.row_group) a.o.row_group[i] = group;
     if (a.o.row_m0) a.o.row_m0[i] = (int32_t)m;
     if (a.o.row_load) a.o.row_load[i] = load;
+    return z;
 }
 
 // ------------------------------------------------------------------ Alg.2 pieces
@@ -176,7 +180,8 @@ __device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, 
                                 Acc &acc, int *nl_out, int *nwhole_out) {
     int nl = 0, nwhole = 0;
     const uint32_t M = g.M;
-    if (g.variant != DAGRT_VAR_NOPARA) {
+    // no SMs left (S = 0, so also WS = 0): every variant stops at its first candidate
+    if (g.variant != DAGRT_VAR_NOPARA && S0 > 0) {
         uint32_t S = S0;
         uint64_t WS = R * (uint64_t)S0;  // Eq.6
         bool stop = false;
@@ -225,7 +230,8 @@ __device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, 
                         a.o.seg_m[g.n0 + s] = (int32_t)mu;
                         a.o.seg_group[g.n0 + s] = j;
                     }
-                    write_row(a, g, acc.nrows++, g.V + s, u, j, (uint32_t)p, k, mu, exec_time(p, k, mu, M));
+                    acc.lastr = acc.nrows;
+                    acc.lastz = write_row(a, g, acc.nrows++, g.V + s, u, j, (uint32_t)p, k, mu, exec_time(p, k, mu, M));
                     ws.rem[u] = load - (uint32_t)p;
                     ws.lst[nl++] = g.V + s;
                     stop = true;
@@ -233,13 +239,19 @@ __device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, 
                 }
                 ws.st[u] |= ST_LAUNCH;
                 ws.mm[u] = (uint16_t)mu;
-                write_row(a, g, acc.nrows++, u, u, j, load, k, mu, c);
+                acc.lastr = acc.nrows;
+                acc.lastz = write_row(a, g, acc.nrows++, u, u, j, load, k, mu, c);
                 ws.lst[nl++] = u;
                 nwhole++;
             }
         }
     }
-    if (a.plan && acc.nrows - 1 < 2 * g.V) a.plan[g.rbase + acc.nrows - 1].z |= 1u << 24;  // last row of pi_j
+    if (a.plan && acc.nrows - 1 < 2 * g.V) {  // mark the last row of pi_j
+        if (acc.lastr == acc.nrows - 1)
+            a.plan[g.rbase + acc.nrows - 1].z = acc.lastz | (1u << 24);  // a plain store: no read back
+        else
+            a.plan[g.rbase + acc.nrows - 1].z |= 1u << 24;
+    }
     if (acc.nrows > 2 * g.V || acc.nseg > g.V) acc.err = true;
     *nl_out = nl;
     *nwhole_out = nwhole;
@@ -299,7 +311,8 @@ __device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int
                 const uint64_t c = x == ws.load[v] ? ws.cfull[v] : exec_time(x, ws.kk[v], m, M);
                 R = c;
                 vR = v;
-                write_row(a, g, acc.nrows++, v, v, j, x, ws.kk[v], m, c);
+                acc.lastr = acc.nrows;
+                acc.lastz = write_row(a, g, acc.nrows++, v, v, j, x, ws.kk[v], m, c);
             }
         } else {
             uint64_t Wg = 0;
@@ -350,7 +363,8 @@ __device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int
                         R = c;
                         vR = v;
                     }
-                    write_row(a, g, acc.nrows++, v, v, j, x, ws.kk[v], m, c);
+                    acc.lastr = acc.nrows;
+                    acc.lastz = write_row(a, g, acc.nrows++, v, v, j, x, ws.kk[v], m, c);
                 }
             }
         }
@@ -476,6 +490,7 @@ __device__ void group_team(const Team<NT> &tm, const Ws &ws, const SchedArgs &a,
     tm.sync();
     if (lead) {
         acc.nrows = nrows;
+        acc.lastr = -1;  // the members' rows were written by the team
         int nl, nwhole;
         launch_parallel(ws, a, g, j, R, M - (uint32_t)sum_m, acc, &nl, &nwhole);
         extra_edges(ws, a, g, j, vR, (int)np, nl, nwhole, acc);
@@ -902,6 +917,8 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     acc.nseg = 0;
     acc.nrel = nsrc;
     acc.err = false;
+    acc.lastr = -1;
+    acc.lastz = 0;
     constexpr int kSerialMax = NT == 32 ? 8 : 32;  // larger groups use the whole team
     for (int j = 0; j < G;) {
         int j1 = j;
