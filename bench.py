@@ -100,6 +100,24 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def rank_seed(rank: int) -> int:
+    """Seed of rank `rank`'s batch: every rank schedules its own batch of the same
+    distribution (weak scaling, no collective on the data path)."""
+    from paper_2602_20826_gb300 import workloads as wl
+    return wl.BASE_SEED + 2 + 1000 * rank
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank floats over all ranks (the slowest rank's time);
+    `dist` is None on a single rank."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -380,7 +398,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    batch = wl.config(2, seed=wl.BASE_SEED + 2 + 1000 * rank)
+    batch = wl.config(2, seed=rank_seed(rank))
     stream = torch.cuda.current_stream()
     ctx = Context(local, stream.cuda_stream)
     keys = ("node_off", "edge_off", "row_ptr", "col", "wcet", "k64")
@@ -423,10 +441,7 @@ def main():
     clk = clocks.stop()
     t_step = sum(a.elapsed_time(b) for a, b in step_ev) / 1e3  # seconds, K steps
     t_kern = sum(a.elapsed_time(b) for a, b in kern_ev) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_step, t_kern], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_kern = float(tt[0]), float(tt[1])
+    t_step, t_kern = max_over_ranks([t_step, t_kern], dist, "cuda")
     ok = bool((out["status"] == 0).all().item())
     gpu_bounds = out["bound"].cpu().numpy()
 
@@ -453,10 +468,7 @@ def main():
         r = e2e_step()
         e2e_sum += time.perf_counter() - ta
     barrier()
-    if dist is not None:
-        tt = torch.tensor([e2e_sum], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_sum = float(tt[0])
+    e2e_sum = max_over_ranks([e2e_sum], dist, "cuda")[0]
     ok = ok and bool((r["status"] == 0).all()) and np.array_equal(r["bound"], gpu_bounds)
 
     peak, peak_kind = _peaks()

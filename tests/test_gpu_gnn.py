@@ -249,3 +249,25 @@ def test_gain_of_training(ctx):
     plain = lev.search([0, 1, 2, 3], 64, [1, 2, 4, 8, 16, 32], 7)["best_bound"]
     got = model.propose(lev, 16)["best_bound"]
     assert np.all(got <= paper) and np.all(got <= plain)
+
+
+def test_propose_on_large_layered_dags(ctx):
+    """Config-5 DAGs (thousands of nodes, CTA-team schedules): every proposal's bound is
+    exact and the winner is never worse than the paper schedule."""
+    from paper_2602_20826_gb300.dagrt import Model
+    b = wl.config(5, n_dags=3)
+    lb = ctx.load(b)
+    model = Model(ctx, [1, 2, 4, 8, 16, 32, 64, 148], seed=9)
+    res = model.propose(lb, 16, want_all=True, want_m=True)
+    for d in range(b.n_dags):
+        rc, plan = oracle.schedule_dag_of(b, d, 0)
+        assert rc == 0
+        a = 2 * int(b.node_off[d])
+        rows = res["cand_m"][a:a + plan["n_rows"]]
+        want = [oracle.bound_plan(plan, b.M, None if c == 0 else np.ascontiguousarray(rows[:, c]), 1)
+                for c in range(17)]
+        assert np.array_equal(res["out_bound"][d], want), d
+        assert res["best_bound"][d] == min(want) <= plan["bound"]
+        assert np.array_equal(res["best_m"][a:a + plan["n_rows"]], rows[:, res["best_cand"][d]])
+    model.free()
+    lb.free()
