@@ -243,7 +243,7 @@ int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_
  *               256. Default 256.
  *   chunk_rows  candidate bounds: the plan rows of a DAG are cut into work items of about
  *               this many rows at group ends (Theorem 1's sum splits there); 8 .. 256.
- *               Default 24.
+ *               Default 48.
  *   item_warps  candidate bounds: warps per CTA of the work-item kernel, 1 .. 8. Default 4.
  *   cta_smem    scheduler: k in 1 .. 4 = CTA teams keep their workspace in shared memory
  *               while it takes at most 1/k of a CTA's shared memory (smallest large DAGs

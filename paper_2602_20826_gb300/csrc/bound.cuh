@@ -60,7 +60,7 @@ __host__ __device__ inline int gen_level(uint64_t seed, int64_t d, int64_t c, in
 // cut at a group end, block of 64 candidates): the bound is a sum over groups (Theorem 1),
 // so chunks evaluate independently and their partial sums add up. Chunks are a property of
 // the plan and are built once per plan.
-constexpr int kChunkRows = 24;     // default target rows per work item
+constexpr int kChunkRows = 48;     // default target rows per work item
 constexpr int kMinChunkRows = 8;
 
 // upper bound on the chunks of one plan (every chunk but a DAG's last has >= chunk_rows rows)
