@@ -934,10 +934,11 @@ static int gnn_prepare(dagrt_batch *b, bool train) {
         o.m = G.m;
         int rc = dagrt_schedule(b, DAGRT_VAR_PAPER, &o, DAGRT_PTR_DEVICE);
         if (rc) return rc;
-        CK(gnn_build_graph(b->n_dags, b->node_off, b->edge_off, b->row_ptr, b->col, G.pred_off, G.pred_idx, G.succ_off,
-                           G.succ_idx, G.cursor, ctx->n_sm, ctx->stream), "build message-passing graph");
-        CK(gnn_features(b->n_dags, b->node_off, b->wcet, b->k64, G.level, G.wanc, G.m, graph_of(b), G.x, ctx->n_sm,
-                        ctx->stream), "node features");
+        const int32_t *st0 = b->plan[DAGRT_VAR_PAPER].status;
+        CK(gnn_build_graph(b->n_dags, b->node_off, b->edge_off, b->row_ptr, b->col, st0, G.pred_off, G.pred_idx,
+                           G.succ_off, G.succ_idx, G.cursor, ctx->n_sm, ctx->stream), "build message-passing graph");
+        CK(gnn_features(b->n_dags, b->node_off, b->wcet, b->k64, G.level, G.wanc, G.m, st0, graph_of(b), G.x,
+                        ctx->n_sm, ctx->stream), "node features");
         ctx->launches += 3;
         G.graph = !ctx->capturing;  // a capture only records the build
     }

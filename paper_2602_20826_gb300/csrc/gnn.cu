@@ -26,13 +26,24 @@ __device__ __forceinline__ uint16_t f2bf(float f) {
 // One warp per DAG: global successor CSR, in-degrees, then predecessor lists filled by all
 // lanes and sorted per node (every list in increasing predecessor id: deterministic).
 __global__ void k_gnn_graph(int32_t n_dags, const int64_t *node_off, const int64_t *edge_off,
-                            const int32_t *row_ptr, const int32_t *col, int32_t *pred_off, int32_t *pred_idx,
-                            int32_t *succ_off, int32_t *succ_idx, int32_t *cursor) {
+                            const int32_t *row_ptr, const int32_t *col, const int32_t *status, int32_t *pred_off,
+                            int32_t *pred_idx, int32_t *succ_off, int32_t *succ_idx, int32_t *cursor) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dags; d += warps) {
         const int64_t n0 = node_off[d], e0 = edge_off[d];
         const int V = (int)(node_off[d + 1] - n0);
+        if (status[d] != DAGRT_OK) {  // a DAG the scheduler rejected: its CSR is not trusted
+            for (int v = lane; v < V; v += 32) {
+                succ_off[n0 + v] = (int32_t)e0;
+                pred_off[n0 + v] = (int32_t)e0;
+            }
+            if (lane == 0 && d == n_dags - 1) {
+                pred_off[node_off[n_dags]] = (int32_t)edge_off[n_dags];
+                succ_off[node_off[n_dags]] = (int32_t)edge_off[n_dags];
+            }
+            continue;
+        }
         const int32_t *rp = row_ptr + n0 + d;
         const int32_t *cl = col + e0;
         for (int v = lane; v < V; v += 32) {
@@ -88,13 +99,13 @@ __global__ void k_gnn_graph(int32_t n_dags, const int64_t *node_off, const int64
 }
 
 cudaError_t gnn_build_graph(int32_t n_dags, const int64_t *node_off, const int64_t *edge_off, const int32_t *row_ptr,
-                            const int32_t *col, int32_t *pred_off, int32_t *pred_idx, int32_t *succ_off,
-                            int32_t *succ_idx, int32_t *cursor, int n_sm, cudaStream_t st) {
+                            const int32_t *col, const int32_t *status, int32_t *pred_off, int32_t *pred_idx,
+                            int32_t *succ_off, int32_t *succ_idx, int32_t *cursor, int n_sm, cudaStream_t st) {
     if (n_dags == 0) return cudaSuccess;
     int grid = (n_dags + 7) / 8;
     if (grid > 16 * n_sm) grid = 16 * n_sm;
-    k_gnn_graph<<<grid, 256, 0, st>>>(n_dags, node_off, edge_off, row_ptr, col, pred_off, pred_idx, succ_off,
-                                      succ_idx, cursor);
+    k_gnn_graph<<<grid, 256, 0, st>>>(n_dags, node_off, edge_off, row_ptr, col, status, pred_off, pred_idx,
+                                      succ_off, succ_idx, cursor);
     return cudaGetLastError();
 }
 
@@ -102,13 +113,21 @@ cudaError_t gnn_build_graph(int32_t n_dags, const int64_t *node_off, const int64
 // x = [log2 C^ / 32, k / 64, log2(1 + indeg) / 8, log2(1 + outdeg) / 8, level / depth,
 //      W^anc / sum C^, log2 m / 12 (the paper schedule's SMs), 1, 0 ...] (16 bf16)
 __global__ void k_gnn_features(int32_t n_dags, const int64_t *node_off, const int64_t *wcet, const uint8_t *k64,
-                               const int32_t *level, const int64_t *wanc, const int32_t *m, GnnGraph g,
-                               uint16_t *x) {
+                               const int32_t *level, const int64_t *wanc, const int32_t *m, const int32_t *status,
+                               GnnGraph g, uint16_t *x) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dags; d += warps) {
         const int64_t n0 = node_off[d];
         const int V = (int)(node_off[d + 1] - n0);
+        if (status[d] != DAGRT_OK) {  // no schedule outputs: zero features
+            for (int v = lane; v < V; v += 32) {
+                uint4 *dst = (uint4 *)(x + (n0 + v) * kFeat);
+                dst[0] = make_uint4(0, 0, 0, 0);
+                dst[1] = make_uint4(0, 0, 0, 0);
+            }
+            continue;
+        }
         double tot = 0;
         int depth = 0;
         for (int v = lane; v < V; v += 32) {
@@ -143,12 +162,12 @@ __global__ void k_gnn_features(int32_t n_dags, const int64_t *node_off, const in
 }
 
 cudaError_t gnn_features(int32_t n_dags, const int64_t *node_off, const int64_t *wcet, const uint8_t *k64,
-                         const int32_t *level, const int64_t *wanc, const int32_t *m, GnnGraph g, uint16_t *x,
-                         int n_sm, cudaStream_t st) {
+                         const int32_t *level, const int64_t *wanc, const int32_t *m, const int32_t *status, GnnGraph g,
+                         uint16_t *x, int n_sm, cudaStream_t st) {
     if (n_dags == 0) return cudaSuccess;
     int grid = (n_dags + 7) / 8;
     if (grid > 16 * n_sm) grid = 16 * n_sm;
-    k_gnn_features<<<grid, 256, 0, st>>>(n_dags, node_off, wcet, k64, level, wanc, m, g, x);
+    k_gnn_features<<<grid, 256, 0, st>>>(n_dags, node_off, wcet, k64, level, wanc, m, status, g, x);
     return cudaGetLastError();
 }
 

@@ -43,14 +43,15 @@ struct GnnParams {
     int32_t n_levels;
 };
 
-// graph build: per-DAG CSRs -> global pred/succ CSRs (deterministic order)
+// graph build: per-DAG CSRs -> global pred/succ CSRs (deterministic order); DAGs whose
+// paper schedule failed (status != DAGRT_OK) get no edges
 cudaError_t gnn_build_graph(int32_t n_dags, const int64_t *node_off, const int64_t *edge_off, const int32_t *row_ptr,
-                            const int32_t *col, int32_t *pred_off, int32_t *pred_idx, int32_t *succ_off,
-                            int32_t *succ_idx, int32_t *cursor, int n_sm, cudaStream_t st);
-// features from the batch and the paper schedule's outputs
+                            const int32_t *col, const int32_t *status, int32_t *pred_off, int32_t *pred_idx,
+                            int32_t *succ_off, int32_t *succ_idx, int32_t *cursor, int n_sm, cudaStream_t st);
+// features from the batch and the paper schedule's outputs (zero for failed DAGs)
 cudaError_t gnn_features(int32_t n_dags, const int64_t *node_off, const int64_t *wcet, const uint8_t *k64,
-                         const int32_t *level, const int64_t *wanc, const int32_t *m, GnnGraph g, uint16_t *x,
-                         int n_sm, cudaStream_t st);
+                         const int32_t *level, const int64_t *wanc, const int32_t *m, const int32_t *status,
+                         GnnGraph g, uint16_t *x, int n_sm, cudaStream_t st);
 // one layer: h_out = ReLU(agg(h_in) W + b); kin = 16 or 128
 cudaError_t gnn_layer_fwd(int kin, GnnGraph g, const uint16_t *h_in, const uint16_t *wt, const float *bias,
                           uint16_t *h_out, int32_t *err, int n_sm, cudaStream_t st);

@@ -271,3 +271,35 @@ def test_propose_on_large_layered_dags(ctx):
         assert np.array_equal(res["best_m"][a:a + plan["n_rows"]], rows[:, res["best_cand"][d]])
     model.free()
     lb.free()
+
+
+def test_proposer_with_rejected_dags(ctx):
+    """DAGs the scheduler rejects (cycle, out-of-range successor, malformed row_ptr, bad
+    C^) get no proposals (-1) and do not disturb the others: a valid DAG's logits and
+    proposals are the same alone and inside the malformed batch."""
+    from paper_2602_20826_gb300.dagrt import Model
+    from tests.oracle_checks import random_small_dag
+    rng = np.random.default_rng(5)
+    good = random_small_dag(rng, 40, 0.2, 500)
+    rp, col, w, k = good
+    bad = [(np.array([0, 1, 2, 3], np.int32), np.array([1, 2, 0], np.int32), w[:3], k[:3]),  # cycle
+           (np.array([0, 1, 1, 1], np.int32), np.array([5], np.int32), w[:3], k[:3]),  # out of range
+           (np.array([0, 2, 1, 2], np.int32), np.array([1, 2], np.int32), w[:3], k[:3]),  # row_ptr
+           (np.array([0, 0, 0, 0], np.int32), np.zeros(0, np.int32), np.array([0, 1, 1]), k[:3])]  # C^ = 0
+    mixed = wl.from_dags([bad[0], good, bad[1], bad[2], good, bad[3]], 148)
+    alone = wl.from_dags([good], 148)
+    model = Model(ctx, LEVELS, seed=4)
+    lm, la = ctx.load(mixed), ctx.load(alone)
+    zm, za = model.logits(lm), model.logits(la)
+    o1, o4 = int(mixed.node_off[1]), int(mixed.node_off[4])
+    assert np.array_equal(zm[o1:o1 + 40], za) and np.array_equal(zm[o4:o4 + 40], za)
+    rm, ra = model.propose(lm, 8), model.propose(la, 8)
+    assert list(rm["best_cand"][[0, 2, 3, 5]]) == [-1] * 4 and list(rm["best_bound"][[0, 2, 3, 5]]) == [-1] * 4
+    assert rm["best_bound"][1] == rm["best_bound"][4] == ra["best_bound"][0]
+    labels = np.full(mixed.total_nodes(), -1, np.int8)
+    labels[o1:o1 + 40] = 1
+    loss = model.train_step(lm, labels, 1e-3)
+    assert np.isfinite(loss)
+    model.free()
+    lm.free()
+    la.free()
