@@ -802,7 +802,7 @@ __global__ void __launch_bounds__(128) k_gnn_topk(int32_t n_dags, const int64_t 
     __shared__ int32_t s_dn[4][32 * (kTopkMax - 1)];
     __shared__ uint8_t s_dl[4][32 * (kTopkMax - 1)];
     __shared__ uint32_t s_mask[4][kTopkMax];
-    __shared__ int s_nc[4], s_m[4];
+    __shared__ int s_nc[4];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int K1 = k - 1;
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -842,29 +842,44 @@ __global__ void __launch_bounds__(128) k_gnn_topk(int32_t n_dags, const int64_t 
             s_dl[wib][lane * K1 + i] = i < cnt ? bl[i] : 0;
         }
         __syncwarp();
-        if (lane == 0) {
-            // merge: the K1 smallest over all lanes (ties: lower node, then lower level)
-            float dv[kTopkMax - 1];
-            int32_t dn[kTopkMax - 1];
-            uint8_t dlv[kTopkMax - 1];
-            int m = 0;
-            for (int i = 0; i < K1; i++) {
-                int best = -1;
-                for (int j = 0; j < 32 * K1; j++) {
-                    if (s_dn[wib][j] < 0) continue;
-                    if (best < 0 || s_dv[wib][j] < s_dv[wib][best] ||
-                        (s_dv[wib][j] == s_dv[wib][best] &&
-                         (s_dn[wib][j] < s_dn[wib][best] ||
-                          (s_dn[wib][j] == s_dn[wib][best] && s_dl[wib][j] < s_dl[wib][best]))))
-                        best = j;
-                }
-                if (best < 0) break;
-                dv[m] = s_dv[wib][best];
-                dn[m] = s_dn[wib][best];
-                dlv[m] = s_dl[wib][best];
-                m++;
-                s_dn[wib][best] = -1;
+        // merge: the K1 smallest over all lanes (ties: lower node, then lower level), by a
+        // warp argmin over the heads of the lanes' sorted lists
+        float dv[kTopkMax - 1];
+        int32_t dn[kTopkMax - 1];
+        uint8_t dlv[kTopkMax - 1];
+        int m = 0, hp = 0;
+        for (int i = 0; i < K1; i++) {
+            float hv = __int_as_float(0x7f800000);
+            int32_t hn = 0x7fffffff;
+            int hl = 0xff;
+            if (hp < cnt) {
+                hv = s_dv[wib][lane * K1 + hp];
+                hn = s_dn[wib][lane * K1 + hp];
+                hl = s_dl[wib][lane * K1 + hp];
             }
+            float bvv = hv;
+            int32_t bnn = hn;
+            int bll = hl, bln = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(FULL, bvv, o);
+                const int32_t on = __shfl_xor_sync(FULL, bnn, o);
+                const int ol = __shfl_xor_sync(FULL, bll, o), oln = __shfl_xor_sync(FULL, bln, o);
+                if (ov < bvv || (ov == bvv && (on < bnn || (on == bnn && (ol < bll || (ol == bll && oln < bln)))))) {
+                    bvv = ov;
+                    bnn = on;
+                    bll = ol;
+                    bln = oln;
+                }
+            }
+            if (bnn == 0x7fffffff) break;  // every list is exhausted
+            if (lane == bln) hp++;
+            dv[m] = bvv;
+            dn[m] = bnn;
+            dlv[m] = (uint8_t)bll;
+            m++;
+        }
+        __syncwarp();
+        if (lane == 0) {
             // group-major order: groups in order of first appearance (= smallest delta)
             int gs[kTopkMax], gc[kTopkMax], G = 0, q = 0;
             bool used[kTopkMax - 1];
@@ -936,10 +951,9 @@ __global__ void __launch_bounds__(128) k_gnn_topk(int32_t n_dags, const int64_t 
                 }
             }
             s_nc[wib] = nc;
-            s_m[wib] = m;
         }
         __syncwarp();
-        const int nc = s_nc[wib], m = s_m[wib];
+        const int nc = s_nc[wib];  // m (the merged changes) is the same in every lane
         const int rows = nrows[d];
         const int64_t rbase = 2 * n0;
         for (int r = lane; r < rows; r += 32) {

@@ -122,3 +122,27 @@ def test_work_item_path_long_dags_and_reschedule(ctx):
         assert np.array_equal(ob1[d], ref), (d, np.nonzero(ob1[d] != ref)[0][:5])
         assert bb1[d] == rb and bc1[d] == rc
     lb.free()
+
+
+def test_work_item_path_with_rejected_dags(ctx):
+    """Rejected DAGs (no plan) get -1 bounds and candidate -1 on the work-item path; the
+    others are exact."""
+    rng = np.random.default_rng(31)
+    good = [random_small_dag(rng, int(rng.integers(5, 80)), 0.15, 10**4) for _ in range(6)]
+    w, k = good[0][2], good[0][3]
+    cyc = (np.array([0, 1, 2, 3], np.int32), np.array([1, 2, 0], np.int32), w[:3], k[:3])
+    rng_bad = (np.array([0, 1, 1, 1], np.int32), np.array([7], np.int32), w[:3], k[:3])
+    dags = [good[0], cyc, good[1], good[2], rng_bad, good[3], good[4], cyc, good[5]]
+    b = wl.from_dags(dags, 148)
+    alloc, stride = wl.candidate_allocations(b, 2, 64, [1, 2, 4, 8, 16, 32], seed=3)
+    lb = ctx.load(b)
+    for v in (0, 1):
+        lb.schedule(v, fields=("status",), check=False)
+    ob, bb, bc = lb.bound([0, 1], 64, alloc, stride)
+    for d in range(b.n_dags):
+        if dags[d] is cyc or dags[d] is rng_bad:
+            assert (ob[d] == -1).all() and bb[d] == -1 and bc[d] == -1
+        else:
+            ref, rb, rc = oracle.search_dag(b, d, alloc, stride, 2, 64, [0, 1])
+            assert np.array_equal(ob[d], ref) and bb[d] == rb and bc[d] == rc
+    lb.free()
