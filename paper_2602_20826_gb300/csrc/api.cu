@@ -765,13 +765,9 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
         }
         int rc = ensure_bscr(b, bound_chunk_scratch(b->n_dags, b->total_nodes, n_variants, n_alloc, b->tune.chunk_rows));
         if (rc) return rc;
-        const size_t per_dag = (4 * nd + 255) / 256 * 256;
         char *t = (char *)b->bscr;
-        ch.counter = (uint32_t *)t;        // the kernels' counters share the first 256 bytes
-        ch.wide_n = (int32_t *)(t + 4);
-        t += 256;
-        ch.wide_list = (int32_t *)t;
-        ch.partial = (int32_t *)(t + per_dag);
+        ch.counter = (uint32_t *)t;  // the first 256 bytes
+        ch.partial = (int32_t *)(t + 256);
         ch.warps = b->tune.item_warps;
     }
     int nl = 0;

@@ -235,9 +235,7 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
     uint32_t issued[2] = {0, 0};  // copies issued per stage (thread 0)
     uint32_t landed[2] = {0, 0};  // waits that saw their copy land (thread 0)
 
-    const int n_work = a.dag_list ? *a.dag_list_n : a.n_dags;
-    for (int wi = blockIdx.x; wi < n_work; wi += gridDim.x) {
-        const int d = a.dag_list ? a.dag_list[wi] : wi;
+    for (int d = blockIdx.x; d < a.n_dags; d += gridDim.x) {
         const int64_t rbase = 2 * a.node_off[d];
         int rows_max = 0;
         bool fit = true;  // the 32-bit form is exact for every variant
@@ -418,20 +416,20 @@ static int64_t chunk_items_call(int32_t n_dags, int64_t total_nodes, int32_t n_v
 }
 
 bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes, int chunk_rows) {
-    return !a.gen && a.n_alloc % 64 == 0 && a.n_dags > 0 && !a.dag_list &&
+    return !a.gen && a.n_alloc % 64 == 0 && a.n_dags > 0 &&
            chunk_items_call(a.n_dags, total_nodes, a.n_variants, a.n_alloc, chunk_rows) < (1ll << 30) &&
            2 * total_nodes < (1ll << 31);
 }
 
 size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc, int chunk_rows) {
-    return 256 + ((size_t)(4 * n_dags + 255) / 256 * 256) +
-           (size_t)chunk_items_call(n_dags, total_nodes, n_variants, n_alloc, chunk_rows) * 64 * 4;
+    return 256 + (size_t)chunk_items_call(n_dags, total_nodes, n_variants, n_alloc, chunk_rows) * 64 * 4;
 }
 
-// After the work items (one CTA per DAG): a DAG whose sums fit 32 bits gets its candidate
-// bounds from its items' partial sums (one thread per candidate) and the argmin; any other
-// DAG goes to the list of the 64-bit kernel. Block 0 also resets the work-item counter
-// for the next call.
+// After the work items (one CTA per DAG, one thread per candidate): a DAG whose sums fit 32
+// bits gets its candidate bounds from its items' partial sums; any other DAG (rare: loads
+// of 2^17 ticks and more) is evaluated here in 64-bit arithmetic, each thread walking its
+// candidate's rows; then the argmin. Block 0 also resets the work-item counter for the
+// next call.
 __global__ void __launch_bounds__(256) k_bound_finish(BoundArgs a, ChunkArgs ch) {
     __shared__ int64_t s_cum[kMaxVariantsPerCall + 1];
     __shared__ int s_fit;
@@ -450,23 +448,42 @@ __global__ void __launch_bounds__(256) k_bound_finish(BoundArgs a, ChunkArgs ch)
             for (int v = 0; v < nv; v++)
                 if (a.status[v][d] == DAGRT_OK) fit = fit && (a.pflag[v][d] & 1);
             s_fit = fit;
-            if (!fit) ch.wide_list[atomicAdd(ch.wide_n, 1)] = d;
         }
         __syncthreads();
-        if (!s_fit) {
-            __syncthreads();
-            continue;
-        }
+        const bool fit = s_fit;
         int64_t best_b = 0;
         int32_t best_c = -1;
         for (int c = tid; c < n_cand; c += blockDim.x) {
             const int vi = c / a.n_alloc, cc = c - vi * a.n_alloc;
             int64_t b = -1;
             if (a.status[vi][d] == DAGRT_OK) {
-                const int nch = ch.nchunk[vi][d];
-                const int32_t *pp = ch.partial + (s_cum[vi] + (int64_t)ch.cpre[vi][d] * ncb + (cc >> 6)) * 64 + (cc & 63);
-                b = 0;
-                for (int k = 0; k < nch; k++) b += pp[(int64_t)k * ncb * 64];
+                if (fit) {  // the items' 32-bit partial sums
+                    const int nch = ch.nchunk[vi][d];
+                    const int32_t *pp =
+                        ch.partial + (s_cum[vi] + (int64_t)ch.cpre[vi][d] * ncb + (cc >> 6)) * 64 + (cc & 63);
+                    b = 0;
+                    for (int k = 0; k < nch; k++) b += pp[(int64_t)k * ncb * 64];
+                } else {  // sums that need 64 bits: this thread walks the candidate's rows
+                    const int64_t rbase = 2 * a.node_off[d];
+                    const int rows = a.nrows[vi][d];
+                    uint64_t bound = 0, gmax = 0, gsum = 0;
+                    uint32_t gm = 0;
+                    for (int r = 0; r < rows; r++) {
+                        const uint4 x = a.plan[vi][rbase + r];
+                        const uint32_t k = (x.z >> 16) & 0xffu, m0 = x.z & 0xffffu;
+                        const uint32_t m = a.m_alloc[(rbase + r) * a.stride + c];
+                        const uint64_t cv = m ? exec_time(x.x, k, m, (uint32_t)a.M) : (uint64_t)x.y;
+                        gmax = cv > gmax ? cv : gmax;
+                        gsum += cv;
+                        gm += m ? m : m0;
+                        if (x.z >> 24) {
+                            bound += gm <= (uint32_t)a.M ? gmax : gsum;
+                            gmax = gsum = 0;
+                            gm = 0;
+                        }
+                    }
+                    b = (int64_t)bound;
+                }
                 better(best_b, best_c, b, c);
             }
             if (a.out) a.out[(int64_t)d * n_cand + c] = b;
@@ -510,7 +527,6 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a,
     if (threadIdx.x == 0) {
         s_cum[0] = 0;
         for (int v = 0; v < nv; v++) s_cum[v + 1] = s_cum[v] + (int64_t)ch.cpre[v][a.n_dags] * ncb;
-        if (blockIdx.x == 0) *ch.wide_n = 0;  // filled by k_bound_finish, which runs after this kernel
     }
     __syncthreads();
     const uint32_t total = (uint32_t)s_cum[nv];
@@ -631,7 +647,6 @@ cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cuda
     if (a.n_dags == 0) return cudaSuccess;
     const int n_cand = a.n_variants * a.n_alloc;
     const bool items = ch != nullptr;
-    BoundArgs aw = a;  // the 64-bit kernel: all DAGs, or the list the work items leave
     if (items) {
         // the item counter is zero here: set when the scratch was allocated, and reset by
         // k_bound_finish at the end of every call
@@ -649,8 +664,7 @@ cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cuda
         k_bound_finish<<<g, 256, 0, st>>>(a, *ch);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 2;
-        aw.dag_list = ch->wide_list;
-        aw.dag_list_n = ch->wide_n;
+        return cudaSuccess;  // k_bound_finish evaluated the DAGs that need 64-bit sums
     }
     // candidates per thread: a thread's candidates must never straddle two variants
     const int cpt = a.n_alloc % 4 == 0 ? 4 : (a.n_alloc % 2 == 0 ? 2 : 1);
@@ -674,7 +688,6 @@ cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cuda
                          : (cpt == 4 ? k_bound_tma<4, false, false> : cpt == 2 ? k_bound_tma<2, false, false>
                                                                               : k_bound_tma<1, false, false>);
     for (K kern : {fast, wide}) {
-        if (items && kern == fast) continue;  // the work items took these DAGs
         int per_sm = 0;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
@@ -683,7 +696,7 @@ cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cuda
         int grid = a.n_dags;
         if (grid > per_sm * n_sm) grid = per_sm * n_sm;
         if (kern == wide && grid > 2 * n_sm) grid = 2 * n_sm;  // few DAGs need the 64-bit form
-        kern<<<grid, threads, smem, st>>>(kern == wide ? aw : a, T);
+        kern<<<grid, threads, smem, st>>>(a, T);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++*launches;
     }

@@ -35,9 +35,6 @@ struct BoundArgs {
     int32_t n_levels;
     uint8_t levels[16];
     uint8_t *best_m;                            // [2*total_nodes] winning allocation or NULL
-    // optional DAG list: the kernels evaluate dag_list[0 .. *dag_list_n) only
-    const int32_t *dag_list;
-    const int32_t *dag_list_n;
 };
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014) on a counter
@@ -82,20 +79,19 @@ struct ChunkArgs {
     const int32_t *chunk[kMaxVariantsPerCall], *nchunk[kMaxVariantsPerCall], *cpre[kMaxVariantsPerCall];
     const int4 *item[kMaxVariantsPerCall];
     uint32_t *counter;            // work-item counter
-    int32_t *wide_n;              // DAGs left to the 64-bit kernel ...
-    int32_t *wide_list;           // ... and their ids [n_dags]
     int32_t *partial;             // [items * 64] partial bounds
     int32_t warps;                // warps per CTA of the work-item kernel
 };
 
-// scratch bytes the balanced path needs for a call (counters, wide list, partials)
+// scratch bytes the balanced path needs for a call (counter, partials)
 size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc, int chunk_rows);
 // the call can take the balanced path (materialised candidates, n_alloc % 64 == 0, and few
 // enough work items for 32-bit item ids)
 bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes, int chunk_rows);
 
 // Enqueue the bound kernels; *launches receives the number of kernels enqueued. With ch
-// (and an eligible call), the balanced path takes the DAGs whose sums fit 32 bits.
+// (an eligible call), the balanced path: work items, then k_bound_finish (which also
+// evaluates the DAGs whose sums need 64 bits); else the tile kernels.
 cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cudaStream_t st, int *launches);
 
 }  // namespace dagrt
