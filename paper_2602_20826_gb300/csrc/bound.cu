@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a,
                 }
             }
             __syncwarp();
-#pragma unroll 2
+#pragma unroll 4
             for (int r = 0; r < rn; r++) {
                 const uint32_t w2 = *(const uint16_t *)(cbuf + r * 64 + 2 * lane);
                 const uint32_t z = pbuf[r].z;
