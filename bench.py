@@ -445,6 +445,29 @@ def main():
     ok = bool((out["status"] == 0).all().item())
     gpu_bounds = out["bound"].cpu().numpy()
 
+    # the same schedule call captured once into a CUDA graph and replayed on a resident
+    # batch (the size-class partition of dagrt_load_csr is not repeated per step)
+    lbg = ctx.load(dev, M=batch.M)
+    lbg.schedule(0, out=out)
+    torch.cuda.synchronize()
+    ctx.graph_begin()
+    lbg.schedule(0, out=out)
+    graph = ctx.graph_end()
+    for _ in range(args.warmup):
+        flush.zero_()
+        graph.launch()
+    g_ev = [(E(), E()) for _ in range(args.steps)]
+    for s_ in range(args.steps):
+        flush.zero_()
+        g_ev[s_][0].record(stream)
+        graph.launch()
+        g_ev[s_][1].record(stream)
+    torch.cuda.synchronize()
+    t_graph = max_over_ranks([sum(a.elapsed_time(b) for a, b in g_ev) / 1e3], dist, "cuda")[0]
+    ok = ok and bool((out["status"] == 0).all().item()) and np.array_equal(out["bound"].cpu().numpy(), gpu_bounds)
+    graph.free()
+    lbg.free()
+
     # end to end through the C ABI from pinned host buffers (copies in the timed region)
     host = {k: torch.from_numpy(getattr(batch, k)).pin_memory() for k in keys}
     h2d = sum(int(t.numel() * t.element_size()) for t in host.values()) + 4 * nd  # + size-class lists
@@ -493,6 +516,9 @@ def main():
         "e2e": {"value": world * nd * args.steps / e2e_sum, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "graph_replay": {"value": world * nd * args.steps / t_graph, "unit": UNIT,
+                         "ms_per_step": 1e3 * t_graph / args.steps,
+                         "what": "dagrt_schedule captured in a CUDA graph, replayed on a resident batch"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic("k_sched_warp", "sched.cu"),
                      "kernel": "k_sched_warp (all size classes of one dagrt_schedule call)",
