@@ -289,6 +289,14 @@ int dagrt_graph_end(dagrt_ctx *ctx, dagrt_graph **out);
 int dagrt_graph_launch(dagrt_graph *graph);
 void dagrt_graph_free(dagrt_graph *graph);
 
+/* ---------------------------------------------------------------- failure detection
+ * Every device-side wait of the library (mbarriers of TMA copies and tensor-core MMAs) has
+ * an iteration limit; a wait that gives up makes the call return DAGRT_E_TIMEOUT and leaves
+ * the context usable. dagrt_selftest_wait exercises that path: one CTA waits on a barrier
+ * that nothing arrives on, gives up after `limit` polls and the call returns
+ * DAGRT_E_TIMEOUT (DAGRT_OK would mean the wait did not give up). Synchronous. */
+int dagrt_selftest_wait(dagrt_ctx *ctx, uint32_t limit);
+
 /* ---------------------------------------------------------------- learned proposer
  * The paper gives the bound of one allocation (Eq.1, Lemma 1, Theorem 1) but no way to
  * choose among the many allocations of a DAG beyond the Eq.5 heuristic of Alg.2. The
@@ -327,6 +335,13 @@ void dagrt_model_free(dagrt_model *model);
 /* Host copy of the parameters out (get != NULL) and/or in (set != NULL; set is applied
  * first), dagrt_model_n_params() floats each. Synchronous. */
 int dagrt_model_params(dagrt_model *model, float *get, const float *set);
+
+/* The whole training state, for checkpoints: parameters, Adam's first and second moments
+ * (3 * dagrt_model_n_params() floats, in that order) and the step count. set (may be NULL)
+ * is applied first with set_step (>= 0); get and get_step (may be NULL) receive the state.
+ * Training resumed from a state continues exactly as the uninterrupted run. Synchronous. */
+int dagrt_model_state(dagrt_model *model, float *get, int32_t *get_step, const float *set,
+                      int32_t set_step);
 
 /* Logits of every kernel of the batch: logits[(node_off[d] + i) * n_levels + l]. The first
  * call on a batch also runs the paper schedule (variant 0) for the features. */

@@ -10,12 +10,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dagrt.h"
 #include "bound.cuh"
 #include "gnn.cuh"
 #include "sched.cuh"
 
 using namespace dagrt;
+
+// NVTX range around a library call (visible in Nsight tools; free when none is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Device buffers are recycled through a per-context pool (exact-size free lists), so a
 // batch that is loaded and freed every step allocates nothing after the first step.
@@ -371,6 +379,7 @@ static int partition_classes(dagrt_batch *b) {
 int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, const int64_t *edge_off,
                    const int32_t *row_ptr, const int32_t *col, const int64_t *wcet, const uint8_t *k64,
                    int32_t M, uint32_t flags, dagrt_batch **out) {
+    NvtxRange nvtx_range_("dagrt_load_csr");
     if (!ctx) return DAGRT_E_INVAL;
     if (!out) return fail(ctx, DAGRT_E_INVAL, "dagrt_load_csr: out is NULL");
     *out = nullptr;
@@ -548,6 +557,7 @@ static int ensure_tmp(dagrt_batch *b, size_t bytes) {
 }
 
 extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_schedule_out *out, uint32_t flags) {
+    NvtxRange nvtx_range_("dagrt_schedule");
     if (!b) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (variant < 0 || variant >= DAGRT_N_VARIANTS)
@@ -685,6 +695,7 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
 extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *variant_ids, int32_t n_alloc,
                            const uint8_t *m_alloc, int64_t cand_stride, int64_t *out_bound, int64_t *best_bound,
                            int32_t *best_cand, uint32_t flags) {
+    NvtxRange nvtx_range_("dagrt_bound");
     if (!b) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (flags & ~DAGRT_PTR_DEVICE) return fail(ctx, DAGRT_E_INVAL, "dagrt_bound: unknown flags 0x%x", flags);
@@ -787,6 +798,7 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
 // ------------------------------------------------------------------ search
 extern "C" int dagrt_search(dagrt_batch *b, const dagrt_search_cfg *cfg, int64_t *out_bound, int64_t *best_bound,
                             int32_t *best_cand, uint8_t *best_m, uint32_t flags) {
+    NvtxRange nvtx_range_("dagrt_search");
     if (!b) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (!cfg) return fail(ctx, DAGRT_E_INVAL, "dagrt_search: cfg is NULL");
@@ -1044,7 +1056,31 @@ extern "C" int dagrt_model_params(dagrt_model *md, float *get, const float *set)
     return DAGRT_OK;
 }
 
+extern "C" int dagrt_model_state(dagrt_model *md, float *get, int32_t *get_step, const float *set,
+                                 int32_t set_step) {
+    if (!md) return DAGRT_E_INVAL;
+    dagrt_ctx *ctx = md->ctx;
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_model_state")) return rc;
+    if (set && set_step < 0) return fail(ctx, DAGRT_E_INVAL, "dagrt_model_state: negative step");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t n = ParamLayout::total, bytes = n * 4;
+    float *dev[3] = {md->p, md->m, md->v};
+    if (set) {
+        for (int i = 0; i < 3; i++)
+            CK(cudaMemcpyAsync(dev[i], set + i * n, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy state");
+        CK(gnn_refresh(md->p, md->wt, md->wb, ctx->stream), "refresh");
+        md->step = set_step;
+    }
+    if (get)
+        for (int i = 0; i < 3; i++)
+            CK(cudaMemcpyAsync(get + i * n, dev[i], bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy state");
+    if (get_step) *get_step = md->step;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return DAGRT_OK;
+}
+
 extern "C" int dagrt_model_logits(dagrt_batch *b, dagrt_model *md, float *logits, uint32_t flags) {
+    NvtxRange nvtx_range_("dagrt_model_logits");
     if (!b || !md) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (md->ctx != ctx) return fail(ctx, DAGRT_E_INVAL, "dagrt_model_logits: model of another context");
@@ -1106,6 +1142,7 @@ static int gnn_grad(dagrt_batch *b, dagrt_model *md, const int8_t *labels, float
 }
 
 extern "C" int dagrt_model_grad(dagrt_batch *b, dagrt_model *md, const int8_t *labels, float *grads, float *loss) {
+    NvtxRange nvtx_range_("dagrt_model_grad");
     if (!b || !md || !labels) return b ? fail(b->ctx, DAGRT_E_INVAL, "dagrt_model_grad: NULL argument") : DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (int rc = refuse_in_capture(ctx, true, "dagrt_model_grad")) return rc;
@@ -1126,6 +1163,7 @@ extern "C" int dagrt_model_grad(dagrt_batch *b, dagrt_model *md, const int8_t *l
 }
 
 extern "C" int dagrt_train_step(dagrt_batch *b, dagrt_model *md, const int8_t *labels, float lr, float *loss) {
+    NvtxRange nvtx_range_("dagrt_train_step");
     if (!b || !md || !labels) return b ? fail(b->ctx, DAGRT_E_INVAL, "dagrt_train_step: NULL argument") : DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (int rc = refuse_in_capture(ctx, true, "dagrt_train_step")) return rc;
@@ -1142,6 +1180,7 @@ extern "C" int dagrt_train_step(dagrt_batch *b, dagrt_model *md, const int8_t *l
 
 extern "C" int dagrt_propose(dagrt_batch *b, dagrt_model *md, int32_t k, int64_t *out_bound, uint8_t *cand_m,
                              int64_t *best_bound, int32_t *best_cand, uint8_t *best_m, uint32_t flags) {
+    NvtxRange nvtx_range_("dagrt_propose");
     if (!b || !md) return b ? fail(b->ctx, DAGRT_E_INVAL, "dagrt_propose: model is NULL") : DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (md->ctx != ctx) return fail(ctx, DAGRT_E_INVAL, "dagrt_propose: model of another context");
@@ -1275,6 +1314,7 @@ static int time_call(dagrt_ctx *ctx, int reps, F call, float *ms) {
 
 extern "C" int dagrt_autotune_schedule(dagrt_batch *b, int32_t variant, int32_t reps, dagrt_tuning *chosen,
                                        float *best_ms) {
+    NvtxRange nvtx_range_("dagrt_autotune_schedule");
     if (!b) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (int rc = refuse_in_capture(ctx, true, "dagrt_autotune_schedule")) return rc;
@@ -1308,6 +1348,7 @@ extern "C" int dagrt_autotune_schedule(dagrt_batch *b, int32_t variant, int32_t 
 extern "C" int dagrt_autotune_bound(dagrt_batch *b, int32_t n_variants, const int32_t *variant_ids, int32_t n_alloc,
                                     const uint8_t *m_alloc, int64_t cand_stride, int32_t reps, dagrt_tuning *chosen,
                                     float *best_ms) {
+    NvtxRange nvtx_range_("dagrt_autotune_bound");
     if (!b) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = b->ctx;
     if (int rc = refuse_in_capture(ctx, true, "dagrt_autotune_bound")) return rc;
@@ -1401,6 +1442,7 @@ extern "C" int dagrt_graph_end(dagrt_ctx *ctx, dagrt_graph **out) {
 }
 
 extern "C" int dagrt_graph_launch(dagrt_graph *g) {
+    NvtxRange nvtx_range_("dagrt_graph_launch");
     if (!g) return DAGRT_E_INVAL;
     dagrt_ctx *ctx = g->ctx;
     if (int rc = refuse_in_capture(ctx, true, "dagrt_graph_launch")) return rc;
@@ -1418,4 +1460,23 @@ extern "C" void dagrt_graph_free(dagrt_graph *g) {
     dagrt_ctx *ctx = g->ctx;
     delete g;
     ctx_unref(ctx);
+}
+
+// ------------------------------------------------------------------ failure detection
+extern "C" int dagrt_selftest_wait(dagrt_ctx *ctx, uint32_t limit) {
+    if (!ctx) return DAGRT_E_INVAL;
+    if (int rc = refuse_in_capture(ctx, true, "dagrt_selftest_wait")) return rc;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int32_t *word = nullptr;
+    CK(ctx->pool.get((void **)&word, 256), "allocate error word");
+    int32_t h = 0;
+    cudaError_t e = cudaMemsetAsync(word, 0, sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = bound_selftest_wait(limit, word, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, word, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    ctx->pool.put(word, 256);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "self-test wait");
+    ctx->launches++;
+    if (h) return fail(ctx, h, "dagrt_selftest_wait: the wait gave up after %u polls (as it should)", limit);
+    return DAGRT_OK;
 }

@@ -58,11 +58,28 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// bounded wait on a stage; false after kSpinLimit polls
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; i++)
+// bounded wait on a stage; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kSpinLimit) {
+    for (uint32_t i = 0; i < limit; i++)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+__global__ void k_selftest_wait(uint32_t limit, int32_t *word) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // nothing arrives: the wait must give up and report, leaving the CTA free to exit
+    const bool ok = mbar_wait(&bar, 0, limit);
+    if (!ok && threadIdx.x == 0) atomicExch(word, DAGRT_E_TIMEOUT);
+}
+
+cudaError_t bound_selftest_wait(uint32_t limit, int32_t *word, cudaStream_t st) {
+    k_selftest_wait<<<1, 32, 0, st>>>(limit, word);
+    return cudaGetLastError();
 }
 
 // argmin helper: smaller bound wins, then the smaller candidate id

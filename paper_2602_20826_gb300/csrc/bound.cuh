@@ -89,6 +89,10 @@ size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_varian
 // enough work items for 32-bit item ids)
 bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes, int chunk_rows);
 
+// One CTA waits on an mbarrier that nothing arrives on, with the kernels' bounded wait,
+// giving up after `limit` polls: *word = DAGRT_E_TIMEOUT (the failure path of every wait).
+cudaError_t bound_selftest_wait(uint32_t limit, int32_t *word, cudaStream_t st);
+
 // Enqueue the bound kernels; *launches receives the number of kernels enqueued. With ch
 // (an eligible call), the balanced path: work items, then k_bound_finish (which also
 // evaluates the DAGs whose sums need 64 bits); else the tile kernels.

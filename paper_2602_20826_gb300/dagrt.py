@@ -72,6 +72,8 @@ dagrt_model_n_params = _sig("dagrt_model_n_params", C.c_int64, [])
 dagrt_model_create = _sig("dagrt_model_create", C.c_int, [_vp, C.c_int32, _vp, C.c_uint64, C.POINTER(_vp)])
 dagrt_model_free = _sig("dagrt_model_free", None, [_vp])
 dagrt_model_params = _sig("dagrt_model_params", C.c_int, [_vp, _vp, _vp])
+dagrt_model_state = _sig("dagrt_model_state", C.c_int, [_vp, _vp, C.POINTER(C.c_int32), _vp, C.c_int32])
+dagrt_selftest_wait = _sig("dagrt_selftest_wait", C.c_int, [_vp, C.c_uint32])
 dagrt_model_logits = _sig("dagrt_model_logits", C.c_int, [_vp, _vp, _vp, C.c_uint32])
 dagrt_model_grad = _sig("dagrt_model_grad", C.c_int, [_vp, _vp, _vp, _vp, _vp])
 dagrt_train_step = _sig("dagrt_train_step", C.c_int, [_vp, _vp, _vp, C.c_float, _vp])
@@ -147,6 +149,9 @@ class Context:
 
     def set_stream(self, stream):
         self.check(dagrt_set_stream(self.h, stream))
+
+    def last_error(self) -> str:
+        return dagrt_last_error(self.h).decode()
 
     def sync(self):
         self.check(dagrt_sync(self.h))
@@ -385,6 +390,18 @@ class Model:
         st = None if set_to is None else np.ascontiguousarray(set_to, np.float32)
         self.ctx.check(dagrt_model_params(self.h, _ptr(out), _ptr(st)))
         return out
+
+    def state(self):
+        """(parameters, Adam m, Adam v) as one float32 array of 3 * n_params, and the step."""
+        buf = np.zeros(3 * self.n_params, np.float32)
+        step = C.c_int32(0)
+        self.ctx.check(dagrt_model_state(self.h, _ptr(buf), C.byref(step), None, 0))
+        return buf, int(step.value)
+
+    def set_state(self, buf, step: int):
+        buf = np.ascontiguousarray(buf, np.float32)
+        assert buf.size == 3 * self.n_params
+        self.ctx.check(dagrt_model_state(self.h, None, None, _ptr(buf), int(step)))
 
     def logits(self, batch: "LoadedBatch", out=None) -> np.ndarray:
         L = len(self.levels)

@@ -9,8 +9,9 @@ per DAG; a kernel's label is the level of the proposer's level list nearest (in 
 the SMs the winner gives the kernel's own plan row (0 in the winner's column means the
 schedule's own m, Eq.5). DAGs whose schedule failed are unlabelled (-1).
 
-Checkpoints hold the fp32 parameters and the level list (npz); Adam's
-moments are not kept, so a resumed run restarts them.
+Checkpoints (npz) hold the whole training state -- fp32 parameters, Adam's moments, the
+step count -- and the level list; a run resumed from one continues exactly as the
+uninterrupted run would.
 """
 from __future__ import annotations
 
@@ -94,13 +95,14 @@ def train(ctx, model: "dagrt.Model", data, epochs: int, lr: float, log=None):
 
 
 def save(model: "dagrt.Model", path: str, **meta):
-    np.savez(path, params=model.params(), levels=model.levels, **meta)
+    state, step = model.state()
+    np.savez(path, state=state, step=step, levels=model.levels, **meta)
 
 
 def load(ctx, path: str) -> "dagrt.Model":
     z = np.load(path)
     m = dagrt.Model(ctx, z["levels"], seed=0)
-    m.params(set_to=z["params"])
+    m.set_state(z["state"], int(z["step"]))
     return m
 
 

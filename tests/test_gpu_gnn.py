@@ -303,3 +303,30 @@ def test_proposer_with_rejected_dags(ctx):
     model.free()
     lm.free()
     la.free()
+
+
+def test_checkpoint_resume_is_exact(ctx, tmp_path):
+    """Training resumed from a checkpoint (parameters, Adam moments, step) continues bit for
+    bit as the uninterrupted run."""
+    from paper_2602_20826_gb300 import train as T
+    from paper_2602_20826_gb300.dagrt import Model
+    b = _batch(5, 20, 100, 33)
+    lb = ctx.load(b)
+    labels = np.minimum(len(LEVELS) - 1, np.log2(b.wcet.astype(np.float64)) // 2.5).astype(np.int8)
+    a = Model(ctx, LEVELS, seed=2)
+    for _ in range(3):
+        a.train_step(lb, labels, 2e-3)
+    path = str(tmp_path / "ckpt.npz")
+    T.save(a, path)
+    for _ in range(3):
+        a.train_step(lb, labels, 2e-3)
+    b2 = T.load(ctx, path)
+    assert b2.state()[1] == 3
+    for _ in range(3):
+        b2.train_step(lb, labels, 2e-3)
+    sa, na = a.state()
+    sb, nb = b2.state()
+    assert na == nb == 6 and np.array_equal(sa, sb)
+    a.free()
+    b2.free()
+    lb.free()
