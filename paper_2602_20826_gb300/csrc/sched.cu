@@ -374,28 +374,41 @@ __device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int
             int nl, nwhole;
             launch_parallel(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
             extra_edges(ws, a, g, j, vR, np, nl, nwhole, acc);
-            // members and whole launches finish with pi_j
-            for (int i = gb; i < ge + nl; i++) {
-                int v;
-                if (i < ge) {
-                    v = ws.gmem[i];
-                    if (ws.st[v] & ST_DONE) continue;
-                } else {
-                    v = ws.lst[i - ge];
-                    if (v >= g.V) continue;  // a segment: its node is not finished
-                }
-                ws.st[v] = ST_DONE;
-                ws.rem[v] = 0;
-                if (a.o.exec_group) a.o.exec_group[g.n0 + v] = j;
-                ws.relmask[ws.rank[v] >> 6] &= ~(1ull << (ws.rank[v] & 63));
-                ws.tmp[nf++] = v;
-            }
-            acc.nrel -= nf;
+            nf = ge - gb + nl;  // candidates to finish: the members, then the launched parts
             if (a.o.group_R) a.o.group_R[g.n0 + j] = (int64_t)R;
             acc.bound += R;
         }
     }
-    nf = __shfl_sync(FULL, nf, 0);
+    __syncwarp();  // lane 0's shared-memory writes (launch list, states) become visible
+    // members (not finished before) and whole launches finish with pi_j: one lane each
+    const int gb = __shfl_sync(FULL, lane == 0 ? (int)ws.gstart[j] : 0, 0);
+    const int ncand = __shfl_sync(FULL, nf, 0);
+    int nfin = 0;
+    for (int base = 0; base < ncand; base += 32) {
+        const int i = base + lane;
+        int v = -1;
+        if (i < ncand) {
+            const int ge = ws.gstart[j + 1];
+            if (gb + i < ge) {
+                v = ws.gmem[gb + i];
+                if (ws.st[v] & ST_DONE) v = -1;
+            } else {
+                v = ws.lst[gb + i - ge];
+                if (v >= g.V) v = -1;  // a segment: its node is not finished
+            }
+        }
+        const uint32_t fin = __ballot_sync(FULL, v >= 0);
+        if (v >= 0) {
+            ws.st[v] = ST_DONE;
+            ws.rem[v] = 0;
+            if (a.o.exec_group) a.o.exec_group[g.n0 + v] = j;
+            atomicAnd((unsigned long long *)&ws.relmask[ws.rank[v] >> 6], ~(1ull << (ws.rank[v] & 63)));
+            ws.tmp[nfin + __popc(fin & ((1u << lane) - 1))] = v;
+        }
+        nfin += __popc(fin);
+    }
+    if (lane == 0) acc.nrel -= nfin;
+    nf = nfin;
     __syncwarp();
     // ... and release their successors
     int released = 0;

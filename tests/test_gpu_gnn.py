@@ -330,3 +330,23 @@ def test_checkpoint_resume_is_exact(ctx, tmp_path):
     a.free()
     b2.free()
     lb.free()
+
+
+def test_proposer_empty_dags_and_empty_batch(ctx):
+    from paper_2602_20826_gb300.dagrt import Model
+    e = (np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64), np.zeros(0, np.uint8))
+    one = (np.zeros(2, np.int32), np.zeros(0, np.int32), np.array([500], np.int64), np.array([40], np.uint8))
+    b = wl.from_dags([e, one, e], 148)
+    model = Model(ctx, LEVELS, seed=1)
+    lb = ctx.load(b)
+    res = model.propose(lb, 16, want_all=True)
+    assert list(res["best_bound"][[0, 2]]) == [0, 0] and list(res["best_cand"][[0, 2]]) == [0, 0]
+    rc, plan = oracle.schedule_dag_of(b, 1, 0)
+    assert res["best_bound"][1] == min(res["out_bound"][1]) <= plan["bound"]
+    lb.free()
+    lb0 = ctx.load(wl.from_dags([], 148))
+    r0 = model.propose(lb0, 4)
+    assert len(r0["best_bound"]) == 0
+    assert model.logits(lb0).shape == (0, len(LEVELS))
+    lb0.free()
+    model.free()
