@@ -42,6 +42,7 @@ struct Ws {
     int32_t *fcnt, *nround;
     uint64_t *bigk;
     uint16_t *rnd;
+    int32_t *thr, *ovl;  // per over-full block: rank of its M-th head; list of over-full blocks
     // phase D
     uint16_t *gtmp;
     int32_t *gfill;
@@ -107,6 +108,8 @@ __host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec,
     w.nround = (int32_t *)take(4ll * (vc + 1));
     w.bigk = (uint64_t *)take(8ll * (vc + 1));
     w.rnd = (uint16_t *)take(2ll * vc);
+    w.thr = (int32_t *)take(4ll * (vc + 1));
+    w.ovl = (int32_t *)take(4ll * (vc + 1));
     mark();
     off = x0;
     w.gtmp = (uint16_t *)take(2ll * vc);
@@ -799,6 +802,7 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             return;
         }
         bool act = false;
+        if (lead) sc[10] = 0;
         for (int v = tm.t; v < V; v += NT)
             if (ws.st[v] & ST_ACTIVE) {
                 act = true;
@@ -806,17 +810,40 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             }
         if (!tm.any(act)) break;
         tm.sync();
+        // blocks with more heads than SMs keep their M heaviest (Top_M): list them, then
+        // one warp per such block walks the nodes in rank order (W^anc descending) with
+        // ballots until its M-th active head; the heads up to that rank form Top_M
+        for (int b = tm.t; b <= N; b += NT)
+            if (ws.fcnt[b] > (int)M) ws.ovl[atomicAdd((int *)&sc[10], 1)] = b;
+        tm.sync();
+        const int nov = sc[10];
+        for (int q = tm.warp(); q < nov; q += NT / 32) {
+            const int b = ws.ovl[q];
+            int cnt = 0, th = V;
+            for (int base = 0; base < V; base += 32) {
+                const int r = base + tm.lane();
+                bool f = false;
+                if (r < V) {
+                    const int u = ws.byrank[r];
+                    f = (ws.st[u] & ST_ACTIVE) && ws.blk[u] == b;
+                }
+                const uint32_t msk = __ballot_sync(FULL, f);
+                const int c = __popc(msk);
+                if (cnt + c >= (int)M) {  // the M-th head is in these 32 ranks
+                    uint32_t mm = msk;
+                    for (int i = 1; i < (int)M - cnt; i++) mm &= mm - 1;
+                    th = base + __ffs(mm) - 1;
+                    break;
+                }
+                cnt += c;
+            }
+            if (tm.lane() == 0) ws.thr[b] = th;
+        }
+        tm.sync();
         for (int v = tm.t; v < V; v += NT) {
             if (!(ws.st[v] & ST_ACTIVE)) continue;
             const int b = ws.blk[v];
-            bool inT = true;
-            if (ws.fcnt[b] > (int)M) {  // more heads than SMs: keep the M heaviest
-                const int rv = ws.rank[v];
-                int pos = 0;
-                for (int u = 0; u < V; u++)
-                    if ((ws.st[u] & ST_ACTIVE) && ws.blk[u] == b && ws.rank[u] < rv) pos++;
-                inT = pos < (int)M;
-            }
+            const bool inT = ws.fcnt[b] <= (int)M || (int)ws.rank[v] <= ws.thr[b];
             if (inT) {
                 ws.st[v] |= ST_INT;
                 if (ws.load[v] >= M)
