@@ -44,9 +44,10 @@ def _args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="dagrt", choices=["dagrt", "reference"])
-    p.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3-bound", "cfg4-learned"],
+    p.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3-bound", "cfg4-learned", "cfg5"],
                    help="cfg2: the headline step; cfg3-bound: candidate bounds of config 3; "
-                        "cfg4-learned: learned proposal + exact check vs plain search")
+                        "cfg4-learned: learned proposal + exact check vs plain search; "
+                        "cfg5: large layered DAGs, paper schedule + bound and top-16 + check")
     p.add_argument("--train-dags", type=int, default=50000, help="cfg4-learned: training DAGs")
     p.add_argument("--epochs", type=int, default=8, help="cfg4-learned: training epochs")
     p.add_argument("--eval-dags", type=int, default=10000,
@@ -311,6 +312,90 @@ def run_cfg4_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cfg5(args):
+    """Config 5: 200 layered DAGs of 2,000-20,000 nodes. One step = the paper schedule and
+    its bound for every DAG (dagrt_load_csr from device-resident arrays + dagrt_schedule);
+    the line also times dagrt_propose (top-16 + exact check, an untrained network: the
+    time, not the proposals, is measured) on a freshly loaded copy."""
+    import torch
+    import oracle
+    from paper_2602_20826_gb300 import workloads as wl
+    from paper_2602_20826_gb300.dagrt import Context, Model
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = Context(0, stream.cuda_stream)
+    b = wl.config(5)
+    keys = ("node_off", "edge_off", "row_ptr", "col", "wcet", "k64")
+    dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(b, k))).cuda() for k in keys}
+    nd = b.n_dags
+    out = {"bound": torch.zeros(nd, dtype=torch.int64, device="cuda"),
+           "status": torch.zeros(nd, dtype=torch.int32, device="cuda")}
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    steps = max(1, min(args.steps, 5))
+
+    def step():
+        lb = ctx.load(dev, M=b.M)
+        lb.schedule(0, out=out)
+        lb.free()
+
+    step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = ctx.launches()
+    evs = [(E(), E()) for _ in range(steps)]
+    for e0, e1 in evs:
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    launches = (ctx.launches() - l0) // steps
+    t = sum(a.elapsed_time(c) for a, c in evs) / 1e3 / steps
+    model = Model(ctx, [1, 2, 4, 8, 16, 32, 64, 148], seed=wl.BASE_SEED)
+    po = {"best_bound": torch.zeros(nd, dtype=torch.int64, device="cuda"),
+          "best_cand": torch.zeros(nd, dtype=torch.int32, device="cuda")}
+    pt = []
+    for r in range(3):
+        lb = ctx.load(dev, M=b.M)
+        torch.cuda.synchronize()
+        e0, e1 = E(), E()
+        e0.record(stream)
+        model.propose(lb, 16, out=po)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r:
+            pt.append(e0.elapsed_time(e1))
+        lb.free()
+    clk = clocks.stop()
+    ok = bool((out["status"] == 0).all().item()) and bool((po["best_bound"] <= out["bound"]).all().item())
+    gpu_bounds = out["bound"].cpu().numpy()
+    # the oracle on the first DAGs (about args.cpu_seconds of work), parity included
+    ts = time.perf_counter()
+    ns = 0
+    while time.perf_counter() - ts < args.cpu_seconds and ns < nd:
+        bo, st = oracle.schedule_batch(b, dags=[ns])
+        ok = ok and int(bo[0]) == int(gpu_bounds[ns])
+        ns += 1
+    cpu_v = ns / (time.perf_counter() - ts)
+    peak, kind = _peaks()
+    alg = b.input_bytes() + 12 * nd
+    line = {"metric": METRIC, "value": nd / t, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": 1,
+            "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "config 5: 200 layered DAGs, 2,000-20,000 nodes, depth 20-60, widths 1-64 "
+                                   "scaled to V, skip edges p=0.02, lognormal WCET, M=148",
+                       "n_dags": nd, "nodes": b.total_nodes(), "edges": b.total_edges()},
+            "propose_top16_ms": float(np.median(pt)), "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / t / 1e9 / peak, "traffic": None,
+                         "kernel": "dagrt_schedule (CTA teams, global workspaces)", "alg_bytes_per_launch": alg,
+                         "peak_source": f"{kind} hbm_gbs"},
+            "clocks": clk, "status_ok": ok,
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {ns} DAGs of the batch, single thread, parity checked"}}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(batch, seconds: float, gpu_bounds=None):
     """The oracle as it stands, single-threaded on this host, over whole passes of the DAGs
     in order until about `seconds` of CPU time; also checks the GPU bounds of every DAG it
@@ -380,6 +465,9 @@ def main():
         return
     if args.workload == "cfg4-learned":
         run_cfg4_learned(args)
+        return
+    if args.workload == "cfg5":
+        run_cfg5(args)
         return
     if args.warmup < 3:
         args.warmup = 3

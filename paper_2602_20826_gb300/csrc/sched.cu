@@ -18,6 +18,7 @@ namespace dagrt {
 // node state bits
 enum : uint8_t { ST_ACTIVE = 1, ST_INT = 2, ST_SEL = 4, ST_DONE = 8, ST_LAUNCH = 16, ST_JOIN = 32 };
 constexpr uint16_t NONE16 = 0xffff;
+constexpr int kSumWords = 8;  // released-set masks longer than this keep a summary of non-empty words
 
 // ------------------------------------------------------------------ workspace layout
 // Persistent arrays live for the whole DAG; the region after them is overlaid by the
@@ -31,6 +32,7 @@ struct Ws {
     uint16_t *scol; // ... and successor ids
     uint16_t *indeg, *lvl_off, *topo, *rank, *byrank, *blk, *group_of, *gstart, *gmem;
     uint64_t *relmask;
+    uint64_t *relsum;  // bit w: relmask[w] may be non-zero (cleared lazily by the scan)
     int32_t *sc;
     // phase A (+ wanc, kept through phase B)
     uint64_t *wanc, *anc, *planes;
@@ -86,6 +88,7 @@ __host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec,
     w.gstart = (uint16_t *)take(2ll * (vc + 2));
     w.gmem = (uint16_t *)take(2ll * vc);
     w.relmask = (uint64_t *)take(8ll * W);
+    w.relsum = (uint64_t *)take(8ll * ((W + 63) / 64));
     w.sc = (int32_t *)take(4 * 16);
     const int64_t x0 = off;
     int64_t end = off;
@@ -179,7 +182,8 @@ __device__ inline uint32_t write_row(const SchedArgs &a, const Dag &g, int r, in
 // Launch parallel nodes for group j (Alg.2's parallel-launch and segmentation step): released, unfinished nodes outside
 // pi_j in descending W^anc order (lowest rank first). One thread. Returns the number of
 // launched parts (ids in ws.lst; a segment id is >= V) and of whole-node launches.
-__device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, int j, uint64_t R, uint32_t S0,
+template <bool SUM>
+__device__ __forceinline__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, int j, uint64_t R, uint32_t S0,
                                 Acc &acc, int *nl_out, int *nwhole_out) {
     int nl = 0, nwhole = 0;
     const uint32_t M = g.M;
@@ -188,8 +192,24 @@ __device__ void launch_parallel(const Ws &ws, const SchedArgs &a, const Dag &g, 
         uint32_t S = S0;
         uint64_t WS = R * (uint64_t)S0;  // Eq.6
         bool stop = false;
-        for (int w = 0; w < g.W && !stop; w++) {
+        // the mask's words in order (lowest rank first); a long mask (SUM) is walked through
+        // its summary of possibly non-empty words
+        int w = -1, sw = -1;
+        uint64_t sbits = 0;
+        while (!stop) {
+            if constexpr (SUM) {
+                while (!sbits && ++sw < ((g.W + 63) >> 6)) sbits = ws.relsum[sw];
+                if (!sbits) break;
+                w = sw * 64 + __ffsll((long long)sbits) - 1;
+                sbits &= sbits - 1;
+            } else {
+                if (++w >= g.W) break;
+            }
             uint64_t bits = ws.relmask[w];
+            if (SUM && !bits) {  // emptied since it was marked
+                ws.relsum[sw] &= ~(1ull << (w & 63));
+                continue;
+            }
             while (bits) {
                 const int b = __ffsll((long long)bits) - 1;
                 bits &= bits - 1;
@@ -375,7 +395,10 @@ __device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int
             if (a.o.group_R) a.o.group_R[g.n0 + j] = 0;
         } else {
             int nl, nwhole;
-            launch_parallel(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
+            if (g.W > kSumWords)
+                launch_parallel<true>(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
+            else
+                launch_parallel<false>(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
             extra_edges(ws, a, g, j, vR, np, nl, nwhole, acc);
             nf = ge - gb + nl;  // candidates to finish: the members, then the launched parts
             if (a.o.group_R) a.o.group_R[g.n0 + j] = (int64_t)R;
@@ -421,6 +444,8 @@ __device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int
             const int s = g.col[e];
             if (atomicSub(&ws.cnt[s], 1) == 1) {
                 atomicOr((unsigned long long *)&ws.relmask[ws.rank[s] >> 6], 1ull << (ws.rank[s] & 63));
+                if (g.W > kSumWords)
+                    atomicOr((unsigned long long *)&ws.relsum[ws.rank[s] >> 12], 1ull << ((ws.rank[s] >> 6) & 63));
                 released++;
             }
         }
@@ -508,7 +533,10 @@ __device__ void group_team(const Team<NT> &tm, const Ws &ws, const SchedArgs &a,
         acc.nrows = nrows;
         acc.lastr = -1;  // the members' rows were written by the team
         int nl, nwhole;
-        launch_parallel(ws, a, g, j, R, M - (uint32_t)sum_m, acc, &nl, &nwhole);
+        if (g.W > kSumWords)
+            launch_parallel<true>(ws, a, g, j, R, M - (uint32_t)sum_m, acc, &nl, &nwhole);
+        else
+            launch_parallel<false>(ws, a, g, j, R, M - (uint32_t)sum_m, acc, &nl, &nwhole);
         extra_edges(ws, a, g, j, vR, (int)np, nl, nwhole, acc);
         sc[1] = nl;
         sc[6] = 0;
@@ -539,6 +567,8 @@ __device__ void group_team(const Team<NT> &tm, const Ws &ws, const SchedArgs &a,
             const int s = g.col[e];
             if (atomicSub(&ws.cnt[s], 1) == 1) {
                 atomicOr((unsigned long long *)&ws.relmask[ws.rank[s] >> 6], 1ull << (ws.rank[s] & 63));
+                if (g.W > kSumWords)
+                    atomicOr((unsigned long long *)&ws.relsum[ws.rank[s] >> 12], 1ull << ((ws.rank[s] >> 6) & 63));
                 atomicAdd((int *)&sc[7], 1);
             }
         }
@@ -782,6 +812,18 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         ws.bigk[b] = 0;
     }
     tm.sync();
+    // a block of more than M nodes may have more than M heads in a round (Top_M below)
+    bool bigblk = false;
+    if (V > (int)M) {
+        for (int v = tm.t; v < V; v += NT) atomicAdd(&ws.fcnt[ws.blk[v]], 1);
+        tm.sync();
+        for (int b = tm.t; b <= N; b += NT) {
+            bigblk |= ws.fcnt[b] > (int)M;
+            ws.fcnt[b] = 0;
+        }
+        bigblk = tm.any(bigblk);
+        tm.sync();
+    }
     for (int u = tm.t; u < V; u += NT)
         for (int e = rp[u]; e < rp[u + 1]; e++)
             if (ws.blk[col[e]] == ws.blk[u]) atomicAdd(&ws.cnt[col[e]], 1);
@@ -810,13 +852,18 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             }
         if (!tm.any(act)) break;
         tm.sync();
+        bool over = false;  // a block with more than M heads (only in a block of more than M nodes)
+        if (bigblk)
+            for (int b = tm.t; b <= N; b += NT) over |= ws.fcnt[b] > (int)M;
+        over = bigblk && tm.any(over);
         // blocks with more heads than SMs keep their M heaviest (Top_M): list them, then
         // one warp per such block walks the nodes in rank order (W^anc descending) with
         // ballots until its M-th active head; the heads up to that rank form Top_M
-        for (int b = tm.t; b <= N; b += NT)
-            if (ws.fcnt[b] > (int)M) ws.ovl[atomicAdd((int *)&sc[10], 1)] = b;
-        tm.sync();
-        const int nov = sc[10];
+        if (over)
+            for (int b = tm.t; b <= N; b += NT)
+                if (ws.fcnt[b] > (int)M) ws.ovl[atomicAdd((int *)&sc[10], 1)] = b;
+        if (over) tm.sync();
+        const int nov = over ? sc[10] : 0;
         for (int q = tm.warp(); q < nov; q += NT / 32) {
             const int b = ws.ovl[q];
             int cnt = 0, th = V;
@@ -839,7 +886,7 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             }
             if (tm.lane() == 0) ws.thr[b] = th;
         }
-        tm.sync();
+        if (over) tm.sync();
         for (int v = tm.t; v < V; v += NT) {
             if (!(ws.st[v] & ST_ACTIVE)) continue;
             const int b = ws.blk[v];
@@ -930,12 +977,17 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     }
     nsrc = (int)tm.sum(nsrc);
     for (int w = tm.t; w < W; w += NT) ws.relmask[w] = 0;
+    for (int w = tm.t; w < (W + 63) / 64; w += NT) ws.relsum[w] = 0;
     tm.sync();
     // released set as a bit mask over ranks (W^anc descending), so the next parallel
-    // node to consider is always the lowest set bit
+    // node to consider is always the lowest set bit; relsum marks its possibly non-empty
+    // words
     for (int v = tm.t; v < V; v += NT)
-        if (ws.indeg[v] == 0)
+        if (ws.indeg[v] == 0) {
             atomicOr((unsigned long long *)&ws.relmask[ws.rank[v] >> 6], 1ull << (ws.rank[v] & 63));
+            if (W > kSumWords)
+                atomicOr((unsigned long long *)&ws.relsum[ws.rank[v] >> 12], 1ull << ((ws.rank[v] >> 6) & 63));
+        }
     tm.sync();
 
     Dag g;
