@@ -178,3 +178,20 @@ def test_config5_layered_sampled(ctx):
         assert res["bound"][d] == res["group_R"][n0:n0 + G].sum()
         assert res["bound"][d] >= -(-int(b.wcet[n0:n0 + V].sum()) // b.M)
         assert res["n_rows"][d] == V + res["n_seg"][d]
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_mid_size_dags_mask_summary_and_top_m(ctx, variant):
+    """DAGs of 600-1,500 nodes: released-set masks of 10-24 words (walked through their
+    summary of non-empty words), blocks wider than M (Top_M by rank-order ballots), CTA
+    teams with shared- and global-memory workspaces; every output bit-exact."""
+    b = wl.small_config(4, 6, 600, 1500, seed=61)
+    _check_batch(ctx, b, variant)
+    layered = []
+    rng = np.random.default_rng(62)
+    for _ in range(3):
+        V = int(rng.integers(700, 1400))
+        s, t = wl.layered_edges(rng, V, int(rng.integers(3, 8)), max_width=400)
+        rp, col = wl.csr_from_edges(V, s, t)
+        layered.append((rp, col, wl.wcet_lognormal(rng, V), wl.k64_uniform(rng, V, 0.3)))
+    _check_batch(ctx, wl.from_dags(layered, 148), variant)
