@@ -442,44 +442,74 @@ size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_varian
     return 256 + (size_t)chunk_items_call(n_dags, total_nodes, n_variants, n_alloc, chunk_rows) * 64 * 4;
 }
 
+// Programmatic dependent launch: the work-item kernel lets k_bound_finish start early;
+// k_bound_finish reads what earlier kernels wrote, then waits for the work items to
+// complete (and their stores to be visible) before it touches their partial sums.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // After the work items (one CTA per DAG, one thread per candidate): a DAG whose sums fit 32
 // bits gets its candidate bounds from its items' partial sums; any other DAG (rare: loads
 // of 2^17 ticks and more) is evaluated here in 64-bit arithmetic, each thread walking its
-// candidate's rows; then the argmin. Block 0 also resets the work-item counter for the
+// candidate's rows; then the argmin. The per-DAG metadata of the CTA's first DAG is read
+// before the wait on the work items. Block 0 also resets the work-item counter for the
 // next call.
 __global__ void __launch_bounds__(256) k_bound_finish(BoundArgs a, ChunkArgs ch) {
     __shared__ int64_t s_cum[kMaxVariantsPerCall + 1];
-    __shared__ int s_fit;
+    __shared__ int32_t s_tot[kMaxVariantsPerCall], s_st[kMaxVariantsPerCall], s_nch[kMaxVariantsPerCall],
+        s_cpre[kMaxVariantsPerCall], s_fitv[kMaxVariantsPerCall];
     __shared__ int64_t s_bb[8];
     __shared__ int32_t s_bc[8];
     const int nv = a.n_variants, ncb = a.n_alloc / 64, n_cand = nv * a.n_alloc;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    auto meta = [&](int d) {
+        if (tid < nv) {
+            const int st = a.status[tid][d];
+            s_st[tid] = st;
+            s_nch[tid] = ch.nchunk[tid][d];
+            s_cpre[tid] = ch.cpre[tid][d];
+            s_fitv[tid] = st != DAGRT_OK || (a.pflag[tid][d] & 1);
+        }
+    };
+    if (tid < nv) s_tot[tid] = ch.cpre[tid][a.n_dags];
+    if ((int)blockIdx.x < a.n_dags) meta(blockIdx.x);
+    __syncthreads();
     if (tid == 0) {
         s_cum[0] = 0;
-        for (int v = 0; v < nv; v++) s_cum[v + 1] = s_cum[v] + (int64_t)ch.cpre[v][a.n_dags] * ncb;
-        if (blockIdx.x == 0) *ch.counter = 0u;
+        for (int v = 0; v < nv; v++) s_cum[v + 1] = s_cum[v] + (int64_t)s_tot[v] * ncb;
     }
+    griddep_wait();
+    if (blockIdx.x == 0 && tid == 0) *ch.counter = 0u;
+    __syncthreads();
     for (int d = blockIdx.x; d < a.n_dags; d += gridDim.x) {
-        if (tid == 0) {
-            bool fit = true;
-            for (int v = 0; v < nv; v++)
-                if (a.status[v][d] == DAGRT_OK) fit = fit && (a.pflag[v][d] & 1);
-            s_fit = fit;
+        if (d != (int)blockIdx.x) {
+            meta(d);
+            __syncthreads();
         }
-        __syncthreads();
-        const bool fit = s_fit;
+        bool fit = true;
+        for (int v = 0; v < nv; v++) fit = fit && s_fitv[v];
         int64_t best_b = 0;
         int32_t best_c = -1;
         for (int c = tid; c < n_cand; c += blockDim.x) {
             const int vi = c / a.n_alloc, cc = c - vi * a.n_alloc;
             int64_t b = -1;
-            if (a.status[vi][d] == DAGRT_OK) {
-                if (fit) {  // the items' 32-bit partial sums
-                    const int nch = ch.nchunk[vi][d];
-                    const int32_t *pp =
-                        ch.partial + (s_cum[vi] + (int64_t)ch.cpre[vi][d] * ncb + (cc >> 6)) * 64 + (cc & 63);
-                    b = 0;
-                    for (int k = 0; k < nch; k++) b += pp[(int64_t)k * ncb * 64];
+            if (s_st[vi] == DAGRT_OK) {
+                if (fit) {  // the items' 32-bit partial sums, four loads in flight
+                    const int nch = s_nch[vi];
+                    const int64_t step = (int64_t)ncb * 64;
+                    const int32_t *pp = ch.partial + (s_cum[vi] + (int64_t)s_cpre[vi] * ncb + (cc >> 6)) * 64 + (cc & 63);
+                    int64_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+                    int k = 0;
+                    for (; k + 4 <= nch; k += 4) {
+                        s0 += pp[k * step];
+                        s1 += pp[(k + 1) * step];
+                        s2 += pp[(k + 2) * step];
+                        s3 += pp[(k + 3) * step];
+                    }
+                    for (; k < nch; k++) s0 += pp[k * step];
+                    b = (s0 + s1) + (s2 + s3);
                 } else {  // sums that need 64 bits: this thread walks the candidate's rows
                     const int64_t rbase = 2 * a.node_off[d];
                     const int rows = a.nrows[vi][d];
@@ -524,18 +554,33 @@ __global__ void __launch_bounds__(256) k_bound_finish(BoundArgs a, ChunkArgs ch)
     }
 }
 
+// nonzero iff some byte of w is neither 0 nor a power of two: per byte, (b | 0x80) - 1
+// cannot borrow from the next byte, and its AND with b is 0 exactly for 0 and powers of two
+__device__ __forceinline__ uint32_t bytes_not_pow2(uint32_t w) { return ((w | 0x80808080u) - 0x01010101u) & w; }
+
+// index of the highest set bit, -1 for 0 (PTX bfind)
+__device__ __forceinline__ int high_bit(uint32_t x) {
+    int r;
+    asm("bfind.u32 %0, %1;" : "=r"(r) : "r"(x));
+    return r;
+}
+
 // Persistent warps over the work items. Per item: its rows (64 candidate bytes and the plan
 // row each, at most kSubRows per phase) are staged by cp.async -- the next item's first
-// phase is staged while this one computes -- then each lane builds the {C, m} table of one
-// row: m = 0 (the schedule's own C and m) and m = 1, 2, 4, ..., 128 (the 32-bit shift form;
-// exec_time above M when CHECK_M). Each lane then runs 2 candidates along the rows with
-// table lookups, taking exec_time only for bytes that are not 0 or a power of two; a group
-// of one row adds its C directly. Each item writes 64 partial sums; k_bound_finish adds
-// them up per candidate once every item is done.
+// phase is staged while this one computes. Per phase, lane r handles plan row r: it builds
+// the row's {C, m} table -- m = 0 (the schedule's own C and m) and m = 1, 2, 4, ..., 128
+// (the 32-bit shift form; exec_time above M when CHECK_M) -- and checks whether all 64
+// candidate bytes of the row are 0 or powers of two; two ballots give the phase's
+// group-end and exact-path row masks, and the group starts follow from the ends. Each lane
+// then runs 2 candidates along the rows with table lookups; rows with other bytes take
+// exec_time for those bytes. A group of one row adds its C directly; the first row of a
+// longer group sets its running max / sum / SMs, its last row adds R_j (Lemma 1). Each item
+// writes 64 partial sums; k_bound_finish adds them up per candidate once every item is done.
 template <bool CHECK_M>
 __global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a, ChunkArgs ch) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ int64_t s_cum[kMaxVariantsPerCall + 1];
+    griddep_launch_dependents();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned char *wbase = sm + w * kWarpBytes;
     uint2 *tbuf = (uint2 *)(wbase + 2 * kStageBytes);
@@ -558,7 +603,7 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a,
         vi = 0;
         while ((int64_t)j >= s_cum[vi + 1]) vi++;
         const uint32_t jj = j - (uint32_t)s_cum[vi];
-        const uint32_t q = jj / (uint32_t)ncb;
+        const uint32_t q = ncb == 1 ? jj : jj / (uint32_t)ncb;
         cb = (int)(jj - q * (uint32_t)ncb);
         rec = ch.item[vi][q];
     };
@@ -586,7 +631,7 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a,
         int4 recn = make_int4(0, 0, 0, 0);
         if (jn < total) locate(jn, vn, cbn, recn);
         uint32_t gmax0 = 0, gmax1 = 0, gsum0 = 0, gsum1 = 0, gm0 = 0, gm1 = 0, b0 = 0, b1 = 0;
-        bool first = true;  // chunks start at a group start
+        uint32_t carry = 1u;  // chunks start at a group start
         bool prefetched = false;
         for (int g0 = rec.y; g0 < rec.z; g0 += kSubRows) {
             const int rn = min(kSubRows, rec.z - g0);
@@ -599,7 +644,8 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a,
             }
             const unsigned char *cbuf = wbase + buf * kStageBytes;
             const uint4 *pbuf = (const uint4 *)(cbuf + kSubRows * 64);
-            if (lane < rn) {  // {C, m} table of row `lane`
+            bool endg = false, odd = false;
+            if (lane < rn) {  // {C, m} table, group end and byte check of row `lane`
                 const uint4 x = pbuf[lane];
                 const uint32_t kk = (x.z >> 16) & 0xffu;
                 const uint32_t A1 = x.x * (64u - kk) + 64u, B1 = x.x * kk - 1u;
@@ -611,39 +657,63 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a,
                     if (CHECK_M && (1u << l) > M) v = (uint32_t)exec_time(x.x, kk, 1u << l, M);
                     t[l + 1] = make_uint2(v, 1u << l);
                 }
-            }
-            __syncwarp();
-#pragma unroll 4
-            for (int r = 0; r < rn; r++) {
-                const uint32_t w2 = *(const uint16_t *)(cbuf + r * 64 + 2 * lane);
-                const uint32_t z = pbuf[r].z;
-                const bool last = (z >> 24) != 0;
-                const uint32_t ma = w2 & 0xffu, mb = w2 >> 8;
-                uint2 ta = tbuf[r * 9 + 32 - __clz(ma)], tb = tbuf[r * 9 + 32 - __clz(mb)];
-                if (((w2 | 0x8080u) - 0x0101u) & w2) {  // a byte that is neither 0 nor a power of two
-                    const uint4 x = pbuf[r];
-                    const uint32_t kk = (x.z >> 16) & 0xffu;
-                    if (ma & (ma - 1)) ta = make_uint2((uint32_t)exec_time(x.x, kk, ma, M), ma);
-                    if (mb & (mb - 1)) tb = make_uint2((uint32_t)exec_time(x.x, kk, mb, M), mb);
+                endg = (x.z >> 24) != 0;
+                const uint4 *cw = (const uint4 *)(cbuf + lane * 64);
+                uint32_t acc = 0;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {  // rotated so that 8 lanes hit 8 distinct 16-byte bank groups
+                    const uint4 v = cw[(q + (lane >> 1)) & 3];
+                    acc |= bytes_not_pow2(v.x) | bytes_not_pow2(v.y) | bytes_not_pow2(v.z) | bytes_not_pow2(v.w);
                 }
-                if (first && last) {  // a group of one row: R = C (Lemma 1 either way)
-                    b0 += ta.x;
-                    b1 += tb.x;
-                } else {
-                    gmax0 = max(gmax0, ta.x);
-                    gmax1 = max(gmax1, tb.x);
-                    gsum0 += ta.x;
-                    gsum1 += tb.x;
-                    gm0 += ta.y;
-                    gm1 += tb.y;
-                    if (last) {
-                        b0 += gm0 <= M ? gmax0 : gsum0;
-                        b1 += gm1 <= M ? gmax1 : gsum1;
-                        gmax0 = gmax1 = gsum0 = gsum1 = gm0 = gm1 = 0;
+                odd = acc != 0;
+            }
+            const uint32_t endm = __ballot_sync(FULL, endg);
+            const uint32_t oddm = __ballot_sync(FULL, odd);
+            const uint32_t startm = (endm << 1) | carry;
+            carry = (endm >> (rn - 1)) & 1u;
+            __syncwarp();
+            auto rows = [&](auto exact) {
+#pragma unroll 4
+                for (int r = 0; r < rn; r++) {
+                    const uint32_t w2 = *(const uint16_t *)(cbuf + r * 64 + 2 * lane);
+                    const uint32_t ma = w2 & 0xffu, mb = w2 >> 8;
+                    const uint2 *tr = tbuf + r * 9 + 1;
+                    uint2 ta = tr[high_bit(ma)], tb = tr[high_bit(mb)];
+                    const uint32_t bit = 1u << r;
+                    if (decltype(exact)::value && (oddm & bit)) {
+                        const uint4 x = pbuf[r];
+                        const uint32_t kk = (x.z >> 16) & 0xffu;
+                        if (ma & (ma - 1)) ta = make_uint2((uint32_t)exec_time(x.x, kk, ma, M), ma);
+                        if (mb & (mb - 1)) tb = make_uint2((uint32_t)exec_time(x.x, kk, mb, M), mb);
+                    }
+                    if (startm & bit) {
+                        if (endm & bit) {  // a group of one row: R = C (Lemma 1 either way)
+                            b0 += ta.x;
+                            b1 += tb.x;
+                        } else {
+                            gmax0 = gsum0 = ta.x;
+                            gmax1 = gsum1 = tb.x;
+                            gm0 = ta.y;
+                            gm1 = tb.y;
+                        }
+                    } else {
+                        gmax0 = max(gmax0, ta.x);
+                        gmax1 = max(gmax1, tb.x);
+                        gsum0 += ta.x;
+                        gsum1 += tb.x;
+                        gm0 += ta.y;
+                        gm1 += tb.y;
+                        if (endm & bit) {
+                            b0 += gm0 <= M ? gmax0 : gsum0;
+                            b1 += gm1 <= M ? gmax1 : gsum1;
+                        }
                     }
                 }
-                first = last;
-            }
+            };
+            if (oddm)
+                rows(std::true_type());
+            else
+                rows(std::false_type());
             __syncwarp();
             if (more) stage(buf, vi, cb, g0 + kSubRows, min(rec.z, g0 + 2 * kSubRows));
         }
@@ -678,8 +748,17 @@ cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cuda
         if (per_sm < 1) per_sm = 1;
         kern<<<per_sm * n_sm, warps * 32, smem, st>>>(a, *ch);
         const int g = a.n_dags < 16 * n_sm ? a.n_dags : 16 * n_sm;
-        k_bound_finish<<<g, 256, 0, st>>>(a, *ch);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(g);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if ((e = cudaLaunchKernelEx(&cfg, k_bound_finish, a, *ch)) != cudaSuccess) return e;
         *launches += 2;
         return cudaSuccess;  // k_bound_finish evaluated the DAGs that need 64-bit sums
     }
