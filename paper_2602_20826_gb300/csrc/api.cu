@@ -516,8 +516,8 @@ static int ensure_chunks(dagrt_batch *b, int variant) {
                 cudaSuccess)
             return cuda_fail(ctx, e, "allocate plan chunks");
     }
-    CK(bound_build_chunks(b->n_dags, b->node_off, p.rows, p.nrows, p.status, p.ci, b->tune.chunk_rows, ctx->n_sm,
-                          ctx->stream),
+    CK(bound_build_chunks(b->n_dags, b->node_off, p.rows, p.nrows, p.status, p.pflag, p.ci, b->tune.chunk_rows,
+                          ctx->n_sm, ctx->stream),
        "build plan chunks");
     ctx->launches += 3;
     // a capture only records the build: an eager call after it must build again
@@ -778,7 +778,7 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
         if (rc) return rc;
         char *t = (char *)b->bscr;
         ch.counter = (uint32_t *)t;  // the first 256 bytes
-        ch.partial = (int32_t *)(t + 256);
+        ch.partial = (unsigned char *)(t + 256);
         ch.warps = b->tune.item_warps;
     }
     int nl = 0;

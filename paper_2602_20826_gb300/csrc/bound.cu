@@ -327,6 +327,7 @@ constexpr int kMaxItemWarps = 8;  // warps per CTA of the work-item kernel: Chun
 // per warp: two staging buffers (candidate bytes + plan rows) and one {C, m} table
 constexpr int kStageBytes = kSubRows * 64 + kSubRows * 16;
 constexpr int kWarpBytes = 2 * kStageBytes + kSubRows * 9 * 8;
+constexpr int kPartialBytes = 512;  // partial sums of one work item: 64 x int32, or 64 x int64
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
@@ -401,29 +402,32 @@ __global__ void __launch_bounds__(1024) k_scan_excl(int32_t n, const int32_t *in
     if (tid == 0) out[n] = carry;
 }
 
-// item records {d, first row, end row} in global plan-row numbering
-__global__ void k_fill_items(int32_t n_dags, const int64_t *node_off, const int32_t *nrows, const int32_t *chunk,
-                             const int32_t *nchunk, const int32_t *cpre, int4 *item) {
+// item records {d, first row, end row, flags} in global plan-row numbering; flags bit 0:
+// the DAG's sums fit 32-bit arithmetic
+__global__ void k_fill_items(int32_t n_dags, const int64_t *node_off, const int32_t *nrows, const int32_t *pflag,
+                             const int32_t *chunk, const int32_t *nchunk, const int32_t *cpre, int4 *item) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dags; d += warps) {
         const int64_t rbase = 2 * node_off[d];
         const int nch = nchunk[d];
+        const int flags = nch ? (pflag[d] & 1) : 0;
         for (int k = lane; k < nch; k += 32) {
             const int r0 = chunk[rbase + k], r1 = k + 1 < nch ? chunk[rbase + k + 1] : nrows[d];
-            item[cpre[d] + k] = make_int4(d, (int)(rbase + r0), (int)(rbase + r1), 0);
+            item[cpre[d] + k] = make_int4(d, (int)(rbase + r0), (int)(rbase + r1), flags);
         }
     }
 }
 
 cudaError_t bound_build_chunks(int32_t n_dags, const int64_t *node_off, const uint4 *plan, const int32_t *nrows,
-                               const int32_t *status, const ChunkIndex &ci, int chunk_rows, int n_sm, cudaStream_t st) {
+                               const int32_t *status, const int32_t *pflag, const ChunkIndex &ci, int chunk_rows,
+                               int n_sm, cudaStream_t st) {
     if (n_dags == 0) return cudaMemsetAsync(ci.cpre, 0, sizeof(int32_t), st);
     int grid = (n_dags + 7) / 8;
     if (grid > 16 * n_sm) grid = 16 * n_sm;
     k_plan_chunks<<<grid, 256, 0, st>>>(n_dags, node_off, plan, nrows, status, ci.chunk, ci.nchunk, chunk_rows);
     k_scan_excl<<<1, 1024, 0, st>>>(n_dags, ci.nchunk, ci.cpre);
-    k_fill_items<<<grid, 256, 0, st>>>(n_dags, node_off, nrows, ci.chunk, ci.nchunk, ci.cpre, ci.item);
+    k_fill_items<<<grid, 256, 0, st>>>(n_dags, node_off, nrows, pflag, ci.chunk, ci.nchunk, ci.cpre, ci.item);
     return cudaGetLastError();
 }
 
@@ -439,7 +443,7 @@ bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes, int chunk_row
 }
 
 size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc, int chunk_rows) {
-    return 256 + (size_t)chunk_items_call(n_dags, total_nodes, n_variants, n_alloc, chunk_rows) * 64 * 4;
+    return 256 + (size_t)chunk_items_call(n_dags, total_nodes, n_variants, n_alloc, chunk_rows) * kPartialBytes;
 }
 
 // Programmatic dependent launch: the work-item kernel lets k_bound_finish start early;
@@ -450,90 +454,85 @@ __device__ __forceinline__ void griddep_launch_dependents() {
 }
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// After the work items (one CTA per DAG, one thread per candidate): a DAG whose sums fit 32
-// bits gets its candidate bounds from its items' partial sums; any other DAG (rare: loads
-// of 2^17 ticks and more) is evaluated here in 64-bit arithmetic, each thread walking its
-// candidate's rows; then the argmin. The per-DAG metadata of the CTA's first DAG is read
-// before the wait on the work items. Block 0 also resets the work-item counter for the
-// next call.
-__global__ void __launch_bounds__(256) k_bound_finish(BoundArgs a, ChunkArgs ch) {
-    __shared__ int64_t s_cum[kMaxVariantsPerCall + 1];
-    __shared__ int32_t s_tot[kMaxVariantsPerCall], s_st[kMaxVariantsPerCall], s_nch[kMaxVariantsPerCall],
-        s_cpre[kMaxVariantsPerCall], s_fitv[kMaxVariantsPerCall];
-    __shared__ int64_t s_bb[8];
-    __shared__ int32_t s_bc[8];
+// After the work items, one warp per DAG: lane l adds up the partial sums of candidates 2l
+// and 2l + 1 of each 64-candidate block over the DAG's items (int32 slots, or int64 where
+// the sums need 64 bits), eight items in flight; -1 for a variant whose schedule failed;
+// then the argmin by shuffles. Everything the work items do not write (item counts,
+// statuses, the DAG's chunk counts) is read before the wait on them. Block 0 also resets
+// the work-item counter for the next call.
+__global__ void __launch_bounds__(32) k_bound_finish(BoundArgs a, ChunkArgs ch) {
     const int nv = a.n_variants, ncb = a.n_alloc / 64, n_cand = nv * a.n_alloc;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int lane = threadIdx.x;
+    // lane v < nv: first item of variant slot v (prefix over the slots' item counts)
+    int64_t cum = lane < nv ? (int64_t)ch.cpre[lane][a.n_dags] * ncb : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(FULL, cum, o);
+        if (lane >= o) cum += y;
+    }
+    cum = __shfl_up_sync(FULL, cum, 1);
+    if (lane == 0) cum = 0;
+    int32_t st = 0, nch = 0, cpre = 0, fit = 0;
     auto meta = [&](int d) {
-        if (tid < nv) {
-            const int st = a.status[tid][d];
-            s_st[tid] = st;
-            s_nch[tid] = ch.nchunk[tid][d];
-            s_cpre[tid] = ch.cpre[tid][d];
-            s_fitv[tid] = st != DAGRT_OK || (a.pflag[tid][d] & 1);
+        if (lane < nv) {
+            st = a.status[lane][d];
+            nch = ch.nchunk[lane][d];
+            cpre = ch.cpre[lane][d];
+            fit = a.pflag[lane][d] & 1;
         }
     };
-    if (tid < nv) s_tot[tid] = ch.cpre[tid][a.n_dags];
     if ((int)blockIdx.x < a.n_dags) meta(blockIdx.x);
-    __syncthreads();
-    if (tid == 0) {
-        s_cum[0] = 0;
-        for (int v = 0; v < nv; v++) s_cum[v + 1] = s_cum[v] + (int64_t)s_tot[v] * ncb;
-    }
     griddep_wait();
-    if (blockIdx.x == 0 && tid == 0) *ch.counter = 0u;
-    __syncthreads();
+    if (blockIdx.x == 0 && lane == 0) *ch.counter = 0u;
     for (int d = blockIdx.x; d < a.n_dags; d += gridDim.x) {
-        if (d != (int)blockIdx.x) {
-            meta(d);
-            __syncthreads();
-        }
-        bool fit = true;
-        for (int v = 0; v < nv; v++) fit = fit && s_fitv[v];
+        if (d != (int)blockIdx.x) meta(d);
         int64_t best_b = 0;
         int32_t best_c = -1;
-        for (int c = tid; c < n_cand; c += blockDim.x) {
-            const int vi = c / a.n_alloc, cc = c - vi * a.n_alloc;
-            int64_t b = -1;
-            if (s_st[vi] == DAGRT_OK) {
-                if (fit) {  // the items' 32-bit partial sums, four loads in flight
-                    const int nch = s_nch[vi];
-                    const int64_t step = (int64_t)ncb * 64;
-                    const int32_t *pp = ch.partial + (s_cum[vi] + (int64_t)s_cpre[vi] * ncb + (cc >> 6)) * 64 + (cc & 63);
-                    int64_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-                    int k = 0;
-                    for (; k + 4 <= nch; k += 4) {
-                        s0 += pp[k * step];
-                        s1 += pp[(k + 1) * step];
-                        s2 += pp[(k + 2) * step];
-                        s3 += pp[(k + 3) * step];
-                    }
-                    for (; k < nch; k++) s0 += pp[k * step];
-                    b = (s0 + s1) + (s2 + s3);
-                } else {  // sums that need 64 bits: this thread walks the candidate's rows
-                    const int64_t rbase = 2 * a.node_off[d];
-                    const int rows = a.nrows[vi][d];
-                    uint64_t bound = 0, gmax = 0, gsum = 0;
-                    uint32_t gm = 0;
-                    for (int r = 0; r < rows; r++) {
-                        const uint4 x = a.plan[vi][rbase + r];
-                        const uint32_t k = (x.z >> 16) & 0xffu, m0 = x.z & 0xffffu;
-                        const uint32_t m = a.m_alloc[(rbase + r) * a.stride + c];
-                        const uint64_t cv = m ? exec_time(x.x, k, m, (uint32_t)a.M) : (uint64_t)x.y;
-                        gmax = cv > gmax ? cv : gmax;
-                        gsum += cv;
-                        gm += m ? m : m0;
-                        if (x.z >> 24) {
-                            bound += gm <= (uint32_t)a.M ? gmax : gsum;
-                            gmax = gsum = 0;
-                            gm = 0;
+        for (int v = 0; v < nv; v++) {
+            const int st_v = __shfl_sync(FULL, st, v), nch_v = __shfl_sync(FULL, nch, v);
+            const int cpre_v = __shfl_sync(FULL, cpre, v), fit_v = __shfl_sync(FULL, fit, v);
+            const int64_t cum_v = __shfl_sync(FULL, cum, v);
+            for (int cbk = 0; cbk < ncb; cbk++) {
+                const int c = v * a.n_alloc + cbk * 64 + 2 * lane;
+                int64_t s0 = -1, s1 = -1;
+                if (st_v == DAGRT_OK) {
+                    const int64_t step = (int64_t)ncb * kPartialBytes;
+                    const unsigned char *pp = ch.partial + (cum_v + (int64_t)cpre_v * ncb + cbk) * kPartialBytes;
+                    s0 = s1 = 0;
+                    if (fit_v) {
+                        pp += 8 * lane;
+                        for (int k0 = 0; k0 < nch_v; k0 += 8) {
+                            int2 x[8];
+#pragma unroll
+                            for (int k = 0; k < 8; k++)
+                                x[k] = k0 + k < nch_v ? *(const int2 *)(pp + (k0 + k) * step) : make_int2(0, 0);
+#pragma unroll
+                            for (int k = 0; k < 8; k++) {
+                                s0 += x[k].x;
+                                s1 += x[k].y;
+                            }
+                        }
+                    } else {
+                        pp += 16 * lane;
+                        for (int k0 = 0; k0 < nch_v; k0 += 4) {
+                            longlong2 x[4];
+#pragma unroll
+                            for (int k = 0; k < 4; k++)
+                                x[k] = k0 + k < nch_v ? *(const longlong2 *)(pp + (k0 + k) * step) : make_longlong2(0, 0);
+#pragma unroll
+                            for (int k = 0; k < 4; k++) {
+                                s0 += x[k].x;
+                                s1 += x[k].y;
+                            }
                         }
                     }
-                    b = (int64_t)bound;
+                    better(best_b, best_c, s0, c);
+                    better(best_b, best_c, s1, c + 1);
                 }
-                better(best_b, best_c, b, c);
+                if (a.out) {  // the caller's buffer is only 8-byte aligned
+                    a.out[(int64_t)d * n_cand + c] = s0;
+                    a.out[(int64_t)d * n_cand + c + 1] = s1;
+                }
             }
-            if (a.out) a.out[(int64_t)d * n_cand + c] = b;
         }
         for (int o = 16; o > 0; o >>= 1) {
             const int64_t ob = __shfl_xor_sync(FULL, best_b, o);
@@ -541,16 +540,9 @@ __global__ void __launch_bounds__(256) k_bound_finish(BoundArgs a, ChunkArgs ch)
             better(best_b, best_c, ob, oc);
         }
         if (lane == 0) {
-            s_bb[w] = best_b;
-            s_bc[w] = best_c;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int i = 1; i < (int)(blockDim.x >> 5); i++) better(best_b, best_c, s_bb[i], s_bc[i]);
             if (a.best_bound) a.best_bound[d] = best_c < 0 ? -1 : best_b;
             if (a.best_cand) a.best_cand[d] = best_c;
         }
-        __syncthreads();
     }
 }
 
@@ -567,17 +559,21 @@ __device__ __forceinline__ int high_bit(uint32_t x) {
 
 // Persistent warps over the work items. Per item: its rows (64 candidate bytes and the plan
 // row each, at most kSubRows per phase) are staged by cp.async -- the next item's first
-// phase is staged while this one computes. Per phase, lane r handles plan row r: it builds
-// the row's {C, m} table -- m = 0 (the schedule's own C and m) and m = 1, 2, 4, ..., 128
-// (the 32-bit shift form; exec_time above M when CHECK_M) -- and checks whether all 64
-// candidate bytes of the row are 0 or powers of two; two ballots give the phase's
-// group-end and exact-path row masks, and the group starts follow from the ends. Each lane
-// then runs 2 candidates along the rows with table lookups; rows with other bytes take
-// exec_time for those bytes. A group of one row adds its C directly; the first row of a
-// longer group sets its running max / sum / SMs, its last row adds R_j (Lemma 1). Each item
-// writes 64 partial sums; k_bound_finish adds them up per candidate once every item is done.
+// phase is staged while this one computes.
+//
+// Items whose DAG's sums fit 32 bits: per phase, lane r handles plan row r -- it builds the
+// row's {C, m} table (m = 0: the schedule's own C and m; m = 1, 2, 4, ..., 128: the 32-bit
+// shift form, exec_time above M when CHECK_M) and checks whether all 64 candidate bytes of
+// the row are 0 or powers of two; two ballots give the phase's group-end and exact-path row
+// masks, and the group starts follow from the ends. Each lane then runs 2 candidates along
+// the rows with table lookups; rows with other bytes take exec_time for those bytes. A
+// group of one row adds its C directly; the first row of a longer group sets its running
+// max / sum / SMs, its last row adds R_j (Lemma 1). Other items run their rows in 64-bit
+// arithmetic with exec_time for every byte. Each item writes 64 partial sums (int32 or
+// int64); k_bound_finish adds them up per candidate once every item is done. At most 64
+// registers a thread, so that eight CTAs of four warps fit an SM by registers.
 template <bool CHECK_M>
-__global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a, ChunkArgs ch) {
+__global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs a, ChunkArgs ch) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ int64_t s_cum[kMaxVariantsPerCall + 1];
     griddep_launch_dependents();
@@ -630,96 +626,133 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32) k_bound_items(BoundArgs a,
         int vn = 0, cbn = 0;
         int4 recn = make_int4(0, 0, 0, 0);
         if (jn < total) locate(jn, vn, cbn, recn);
-        uint32_t gmax0 = 0, gmax1 = 0, gsum0 = 0, gsum1 = 0, gm0 = 0, gm1 = 0, b0 = 0, b1 = 0;
-        uint32_t carry = 1u;  // chunks start at a group start
         bool prefetched = false;
-        for (int g0 = rec.y; g0 < rec.z; g0 += kSubRows) {
-            const int rn = min(kSubRows, rec.z - g0);
-            cp_async_wait_all();
-            __syncwarp();
-            const bool more = g0 + kSubRows < rec.z;
-            if (!more && jn < total) {  // stage the next item while this phase computes
-                stage(buf ^ 1, vn, cbn, recn.y, min(recn.z, recn.y + kSubRows));
-                prefetched = true;
-            }
-            const unsigned char *cbuf = wbase + buf * kStageBytes;
-            const uint4 *pbuf = (const uint4 *)(cbuf + kSubRows * 64);
-            bool endg = false, odd = false;
-            if (lane < rn) {  // {C, m} table, group end and byte check of row `lane`
-                const uint4 x = pbuf[lane];
-                const uint32_t kk = (x.z >> 16) & 0xffu;
-                const uint32_t A1 = x.x * (64u - kk) + 64u, B1 = x.x * kk - 1u;
-                uint2 *t = tbuf + lane * 9;
-                t[0] = make_uint2(x.y, x.z & 0xffffu);
-#pragma unroll
-                for (int l = 0; l < 8; l++) {
-                    uint32_t v = ((A1 << l) + B1) >> (l + 6);
-                    if (CHECK_M && (1u << l) > M) v = (uint32_t)exec_time(x.x, kk, 1u << l, M);
-                    t[l + 1] = make_uint2(v, 1u << l);
+        // the item's phases; FIT: 32-bit table path, else 64-bit sums with exec_time
+        auto run_item = [&](auto fitc) {
+            constexpr bool FIT = decltype(fitc)::value;
+            using acc_t = typename std::conditional<FIT, uint32_t, uint64_t>::type;
+            acc_t gmax0 = 0, gmax1 = 0, gsum0 = 0, gsum1 = 0, b0 = 0, b1 = 0;
+            uint32_t gm0 = 0, gm1 = 0;
+            uint32_t carry = 1u;  // chunks start at a group start
+            for (int g0 = rec.y; g0 < rec.z; g0 += kSubRows) {
+                const int rn = min(kSubRows, rec.z - g0);
+                cp_async_wait_all();
+                __syncwarp();
+                const bool more = g0 + kSubRows < rec.z;
+                if (!more && jn < total) {  // stage the next item while this phase computes
+                    stage(buf ^ 1, vn, cbn, recn.y, min(recn.z, recn.y + kSubRows));
+                    prefetched = true;
                 }
-                endg = (x.z >> 24) != 0;
-                const uint4 *cw = (const uint4 *)(cbuf + lane * 64);
-                uint32_t acc = 0;
-#pragma unroll
-                for (int q = 0; q < 4; q++) {  // rotated so that 8 lanes hit 8 distinct 16-byte bank groups
-                    const uint4 v = cw[(q + (lane >> 1)) & 3];
-                    acc |= bytes_not_pow2(v.x) | bytes_not_pow2(v.y) | bytes_not_pow2(v.z) | bytes_not_pow2(v.w);
-                }
-                odd = acc != 0;
-            }
-            const uint32_t endm = __ballot_sync(FULL, endg);
-            const uint32_t oddm = __ballot_sync(FULL, odd);
-            const uint32_t startm = (endm << 1) | carry;
-            carry = (endm >> (rn - 1)) & 1u;
-            __syncwarp();
-            auto rows = [&](auto exact) {
-#pragma unroll 4
-                for (int r = 0; r < rn; r++) {
-                    const uint32_t w2 = *(const uint16_t *)(cbuf + r * 64 + 2 * lane);
-                    const uint32_t ma = w2 & 0xffu, mb = w2 >> 8;
-                    const uint2 *tr = tbuf + r * 9 + 1;
-                    uint2 ta = tr[high_bit(ma)], tb = tr[high_bit(mb)];
-                    const uint32_t bit = 1u << r;
-                    if (decltype(exact)::value && (oddm & bit)) {
-                        const uint4 x = pbuf[r];
+                const unsigned char *cbuf = wbase + buf * kStageBytes;
+                const uint4 *pbuf = (const uint4 *)(cbuf + kSubRows * 64);
+                if constexpr (FIT) {
+                    bool endg = false, odd = false;
+                    if (lane < rn) {  // {C, m} table, group end and byte check of row `lane`
+                        const uint4 x = pbuf[lane];
                         const uint32_t kk = (x.z >> 16) & 0xffu;
-                        if (ma & (ma - 1)) ta = make_uint2((uint32_t)exec_time(x.x, kk, ma, M), ma);
-                        if (mb & (mb - 1)) tb = make_uint2((uint32_t)exec_time(x.x, kk, mb, M), mb);
-                    }
-                    if (startm & bit) {
-                        if (endm & bit) {  // a group of one row: R = C (Lemma 1 either way)
-                            b0 += ta.x;
-                            b1 += tb.x;
-                        } else {
-                            gmax0 = gsum0 = ta.x;
-                            gmax1 = gsum1 = tb.x;
-                            gm0 = ta.y;
-                            gm1 = tb.y;
+                        const uint32_t A1 = x.x * (64u - kk) + 64u, B1 = x.x * kk - 1u;
+                        uint2 *t = tbuf + lane * 9;
+                        t[0] = make_uint2(x.y, x.z & 0xffffu);
+#pragma unroll
+                        for (int l = 0; l < 8; l++) {
+                            uint32_t v = ((A1 << l) + B1) >> (l + 6);
+                            if (CHECK_M && (1u << l) > M) v = (uint32_t)exec_time(x.x, kk, 1u << l, M);
+                            t[l + 1] = make_uint2(v, 1u << l);
                         }
-                    } else {
-                        gmax0 = max(gmax0, ta.x);
-                        gmax1 = max(gmax1, tb.x);
-                        gsum0 += ta.x;
-                        gsum1 += tb.x;
-                        gm0 += ta.y;
-                        gm1 += tb.y;
-                        if (endm & bit) {
+                        endg = (x.z >> 24) != 0;
+                        const uint4 *cw = (const uint4 *)(cbuf + lane * 64);
+                        uint32_t acc = 0;
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {  // rotated: 8 lanes hit 8 distinct 16-byte bank groups
+                            const uint4 v = cw[(q + (lane >> 1)) & 3];
+                            acc |= bytes_not_pow2(v.x) | bytes_not_pow2(v.y) | bytes_not_pow2(v.z) |
+                                   bytes_not_pow2(v.w);
+                        }
+                        odd = acc != 0;
+                    }
+                    const uint32_t endm = __ballot_sync(FULL, endg);
+                    const uint32_t oddm = __ballot_sync(FULL, odd);
+                    const uint32_t startm = (endm << 1) | carry;
+                    carry = (endm >> (rn - 1)) & 1u;
+                    __syncwarp();
+                    auto rows = [&](auto exact) {
+#pragma unroll 4
+                        for (int r = 0; r < rn; r++) {
+                            const uint32_t w2 = *(const uint16_t *)(cbuf + r * 64 + 2 * lane);
+                            const uint32_t ma = w2 & 0xffu, mb = w2 >> 8;
+                            const uint2 *tr = tbuf + r * 9 + 1;
+                            uint2 ta = tr[high_bit(ma)], tb = tr[high_bit(mb)];
+                            const uint32_t bit = 1u << r;
+                            if (decltype(exact)::value && (oddm & bit)) {
+                                const uint4 x = pbuf[r];
+                                const uint32_t kk = (x.z >> 16) & 0xffu;
+                                if (ma & (ma - 1)) ta = make_uint2((uint32_t)exec_time(x.x, kk, ma, M), ma);
+                                if (mb & (mb - 1)) tb = make_uint2((uint32_t)exec_time(x.x, kk, mb, M), mb);
+                            }
+                            if (startm & bit) {
+                                if (endm & bit) {  // a group of one row: R = C (Lemma 1 either way)
+                                    b0 += ta.x;
+                                    b1 += tb.x;
+                                } else {
+                                    gmax0 = gsum0 = ta.x;
+                                    gmax1 = gsum1 = tb.x;
+                                    gm0 = ta.y;
+                                    gm1 = tb.y;
+                                }
+                            } else {
+                                gmax0 = max(gmax0, ta.x);
+                                gmax1 = max(gmax1, tb.x);
+                                gsum0 += ta.x;
+                                gsum1 += tb.x;
+                                gm0 += ta.y;
+                                gm1 += tb.y;
+                                if (endm & bit) {
+                                    b0 += gm0 <= M ? gmax0 : gsum0;
+                                    b1 += gm1 <= M ? gmax1 : gsum1;
+                                }
+                            }
+                        }
+                    };
+                    if (oddm)
+                        rows(std::true_type());
+                    else
+                        rows(std::false_type());
+                } else {  // 64-bit sums: exec_time for every byte
+                    for (int r = 0; r < rn; r++) {
+                        const uint4 x = pbuf[r];
+                        const uint32_t kk = (x.z >> 16) & 0xffu, m0 = x.z & 0xffffu;
+                        const uint32_t w2 = *(const uint16_t *)(cbuf + r * 64 + 2 * lane);
+                        const uint32_t ma = w2 & 0xffu, mb = w2 >> 8;
+                        const uint64_t ca = ma ? exec_time(x.x, kk, ma, M) : (uint64_t)x.y;
+                        const uint64_t cv = mb ? exec_time(x.x, kk, mb, M) : (uint64_t)x.y;
+                        gmax0 = ca > gmax0 ? ca : gmax0;
+                        gmax1 = cv > gmax1 ? cv : gmax1;
+                        gsum0 += ca;
+                        gsum1 += cv;
+                        gm0 += ma ? ma : m0;
+                        gm1 += mb ? mb : m0;
+                        if (x.z >> 24) {
                             b0 += gm0 <= M ? gmax0 : gsum0;
                             b1 += gm1 <= M ? gmax1 : gsum1;
+                            gmax0 = gmax1 = gsum0 = gsum1 = 0;
+                            gm0 = gm1 = 0;
                         }
                     }
                 }
-            };
-            if (oddm)
-                rows(std::true_type());
+                __syncwarp();
+                if (more) stage(buf, vi, cb, g0 + kSubRows, min(rec.z, g0 + 2 * kSubRows));
+            }
+            unsigned char *slot = ch.partial + (size_t)j * kPartialBytes;
+            if constexpr (FIT)
+                *(uint2 *)(slot + 8 * lane) = make_uint2(b0, b1);
             else
-                rows(std::false_type());
-            __syncwarp();
-            if (more) stage(buf, vi, cb, g0 + kSubRows, min(rec.z, g0 + 2 * kSubRows));
-        }
+                *(ulonglong2 *)(slot + 16 * lane) = make_ulonglong2(b0, b1);
+        };
+        if (rec.w & 1)
+            run_item(std::true_type());
+        else
+            run_item(std::false_type());
         if (!prefetched && jn < total) stage(buf ^ 1, vn, cbn, recn.y, min(recn.z, recn.y + kSubRows));
-        // item j's partial sums (garbage for a DAG that needs 64-bit sums: never read)
-        *(uint2 *)(ch.partial + (int64_t)j * 64 + 2 * lane) = make_uint2(b0, b1);
         j = jn;
         vi = vn;
         cb = cbn;
@@ -747,10 +780,10 @@ cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cuda
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         kern<<<per_sm * n_sm, warps * 32, smem, st>>>(a, *ch);
-        const int g = a.n_dags < 16 * n_sm ? a.n_dags : 16 * n_sm;
+        const int g = a.n_dags < 32 * n_sm ? a.n_dags : 32 * n_sm;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(g);
-        cfg.blockDim = dim3(256);
+        cfg.blockDim = dim3(32);
         cfg.dynamicSmemBytes = 0;
         cfg.stream = st;
         cudaLaunchAttribute at[1];

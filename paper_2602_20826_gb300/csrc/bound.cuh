@@ -52,11 +52,11 @@ __host__ __device__ inline int gen_level(uint64_t seed, int64_t d, int64_t c, in
 }
 
 // ---------------------------------------------------------------- balanced work items
-// For materialised candidates (n_alloc a multiple of 64) whose DAG keeps every sum below
-// 2^31, the bound is evaluated per work item = (variant, DAG, chunk of ~kChunkRows plan rows
-// cut at a group end, block of 64 candidates): the bound is a sum over groups (Theorem 1),
-// so chunks evaluate independently and their partial sums add up. Chunks are a property of
-// the plan and are built once per plan.
+// For materialised candidates (n_alloc a multiple of 64), the bound is evaluated per work
+// item = (variant, DAG, chunk of ~kChunkRows plan rows cut at a group end, block of 64
+// candidates): the bound is a sum over groups (Theorem 1), so chunks evaluate independently
+// and their partial sums add up. Chunks are a property of the plan and are built once per
+// plan.
 constexpr int kChunkRows = 48;     // default target rows per work item
 constexpr int kMinChunkRows = 8;
 
@@ -69,17 +69,19 @@ struct ChunkIndex {  // device arrays of one plan
     int32_t *chunk;   // [2*total_nodes]: chunk k of DAG d starts at row chunk[2*node_off[d] + k]
     int32_t *nchunk;  // [n_dags]: 0 where the DAG's schedule failed
     int32_t *cpre;    // [n_dags + 1]: exclusive prefix sum of nchunk
-    int4 *item;       // [cpre[n_dags]]: {d, first global plan row, end global plan row, 0}, DAG-major
+    int4 *item;       // [cpre[n_dags]]: {d, first global plan row, end global plan row, flags}, DAG-major;
+                      // flags bit 0: the DAG's sums fit 32-bit arithmetic
 };
 
 cudaError_t bound_build_chunks(int32_t n_dags, const int64_t *node_off, const uint4 *plan, const int32_t *nrows,
-                               const int32_t *status, const ChunkIndex &ci, int chunk_rows, int n_sm, cudaStream_t st);
+                               const int32_t *status, const int32_t *pflag, const ChunkIndex &ci, int chunk_rows,
+                               int n_sm, cudaStream_t st);
 
 struct ChunkArgs {
     const int32_t *chunk[kMaxVariantsPerCall], *nchunk[kMaxVariantsPerCall], *cpre[kMaxVariantsPerCall];
     const int4 *item[kMaxVariantsPerCall];
     uint32_t *counter;            // work-item counter
-    int32_t *partial;             // [items * 64] partial bounds
+    unsigned char *partial;       // [items * 512 B]: 64 int32 partial bounds (64 int64 where sums need 64 bits)
     int32_t warps;                // warps per CTA of the work-item kernel
 };
 
@@ -94,8 +96,8 @@ bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes, int chunk_row
 cudaError_t bound_selftest_wait(uint32_t limit, int32_t *word, cudaStream_t st);
 
 // Enqueue the bound kernels; *launches receives the number of kernels enqueued. With ch
-// (an eligible call), the balanced path: work items, then k_bound_finish (which also
-// evaluates the DAGs whose sums need 64 bits); else the tile kernels.
+// (an eligible call), the balanced path: work items, then k_bound_finish (sums of the
+// items' partial bounds, argmin); else the tile kernels.
 cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cudaStream_t st, int *launches);
 
 }  // namespace dagrt

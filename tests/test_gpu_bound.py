@@ -92,8 +92,8 @@ def test_unscheduled_variant_is_rejected(ctx):
 def test_work_item_path_arbitrary_bytes(ctx):
     """n_alloc a multiple of 64 takes the balanced work-item kernel (chunks of plan rows cut
     at group ends): any byte value, M below and above 128 (table entries above M), DAGs
-    whose sums need 64 bits mixed in (those go to the 64-bit kernel), one-node DAGs, and
-    repeated calls on the same scratch."""
+    whose sums need 64 bits mixed in (their items run in 64-bit arithmetic), one-node DAGs,
+    and repeated calls on the same scratch."""
     rng = np.random.default_rng(23)
     for M, n_alloc in ((1, 64), (8, 128), (100, 64), (148, 64), (4096, 64)):
         dags = [random_small_dag(rng, int(rng.integers(1, 90)), 0.1, int(rng.choice([10, 10**4, 10**4, 2**32 - 1])))
@@ -144,5 +144,32 @@ def test_work_item_path_with_rejected_dags(ctx):
             assert (ob[d] == -1).all() and bb[d] == -1 and bc[d] == -1
         else:
             ref, rb, rc = oracle.search_dag(b, d, alloc, stride, 2, 64, [0, 1])
+            assert np.array_equal(ob[d], ref) and bb[d] == rb and bc[d] == rc
+    lb.free()
+
+
+def test_work_item_path_empty_dags(ctx):
+    """DAGs without nodes (first, middle, last) get bound 0 for every candidate and
+    candidate 0 as the argmin; their neighbours are exact; a second call on the same
+    scratch gives the same result (the completion counters were left at zero)."""
+    rng = np.random.default_rng(5)
+    e = (np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64), np.zeros(0, np.uint8))
+    good = [random_small_dag(rng, int(rng.integers(2, 60)), 0.1, 10**4) for _ in range(3)]
+    dags = [e, good[0], e, good[1], good[2], e]
+    b = wl.from_dags(dags, 148)
+    alloc, stride = wl.candidate_allocations(b, 2, 64, [1, 2, 4, 8, 16, 32], seed=9)
+    lb = ctx.load(b)
+    for v in (0, 2):
+        lb.schedule(v, fields=("status",))
+    first = lb.bound([0, 2], 64, alloc, stride)
+    again = lb.bound([0, 2], 64, alloc, stride)
+    for x, y in zip(first, again):
+        assert np.array_equal(x, y)
+    ob, bb, bc = first
+    for d in range(b.n_dags):
+        if dags[d] is e:
+            assert (ob[d] == 0).all() and bb[d] == 0 and bc[d] == 0
+        else:
+            ref, rb, rc = oracle.search_dag(b, d, alloc, stride, 2, 64, [0, 2])
             assert np.array_equal(ob[d], ref) and bb[d] == rb and bc[d] == rc
     lb.free()
