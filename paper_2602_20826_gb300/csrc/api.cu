@@ -537,8 +537,9 @@ static int ensure_bscr(dagrt_batch *b, size_t bytes) {
     bytes = (bytes + 255) / 256 * 256;
     CK(ctx->pool.get(&b->bscr, bytes), "allocate bound scratch");
     b->bscr_cap = bytes;
-    // the work-item counter starts at zero; the bound kernels reset it after every call
-    CK(cudaMemsetAsync(b->bscr, 0, 256, ctx->stream), "clear bound scratch");
+    // the work-item counter and the bound accumulators start at zero; every call leaves
+    // them zero
+    CK(cudaMemsetAsync(b->bscr, 0, bytes, ctx->stream), "clear bound scratch");
     return DAGRT_OK;
 }
 
@@ -778,7 +779,7 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
         if (rc) return rc;
         char *t = (char *)b->bscr;
         ch.counter = (uint32_t *)t;  // the first 256 bytes
-        ch.partial = (unsigned char *)(t + 256);
+        ch.acc = (unsigned long long *)(t + 256);
         ch.warps = b->tune.item_warps;
     }
     int nl = 0;

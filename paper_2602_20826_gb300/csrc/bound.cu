@@ -327,7 +327,6 @@ constexpr int kMaxItemWarps = 8;  // warps per CTA of the work-item kernel: Chun
 // per warp: two staging buffers (candidate bytes + plan rows) and one {C, m} table
 constexpr int kStageBytes = kSubRows * 64 + kSubRows * 16;
 constexpr int kWarpBytes = 2 * kStageBytes + kSubRows * 9 * 8;
-constexpr int kPartialBytes = 512;  // partial sums of one work item: 64 x int32, or 64 x int64
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
@@ -443,7 +442,9 @@ bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes, int chunk_row
 }
 
 size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc, int chunk_rows) {
-    return 256 + (size_t)chunk_items_call(n_dags, total_nodes, n_variants, n_alloc, chunk_rows) * kPartialBytes;
+    (void)total_nodes;
+    (void)chunk_rows;
+    return 256 + (size_t)n_dags * n_variants * n_alloc * 8;
 }
 
 // Programmatic dependent launch: the work-item kernel lets k_bound_finish start early;
@@ -454,79 +455,40 @@ __device__ __forceinline__ void griddep_launch_dependents() {
 }
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// After the work items, one warp per DAG: lane l adds up the partial sums of candidates 2l
-// and 2l + 1 of each 64-candidate block over the DAG's items (int32 slots, or int64 where
-// the sums need 64 bits), eight items in flight; -1 for a variant whose schedule failed;
-// then the argmin by shuffles. Everything the work items do not write (item counts,
-// statuses, the DAG's chunk counts) is read before the wait on them. Block 0 also resets
-// the work-item counter for the next call.
+// After the work items, one warp per DAG: the items have added their partial bounds into
+// the DAG's per-candidate accumulators; lane l reads candidates 2l and 2l + 1 of four
+// 64-candidate blocks at a time, writes the bounds (-1 for a variant whose schedule
+// failed), clears the accumulators for the next call and takes the argmin by shuffles. The
+// statuses are read before the wait on the work items. Block 0 also resets the work-item
+// counter.
 __global__ void __launch_bounds__(32) k_bound_finish(BoundArgs a, ChunkArgs ch) {
-    const int nv = a.n_variants, ncb = a.n_alloc / 64, n_cand = nv * a.n_alloc;
+    const int nv = a.n_variants, ncb = a.n_alloc / 64, n_cand = nv * a.n_alloc, nblk = nv * ncb;
     const int lane = threadIdx.x;
-    // lane v < nv: first item of variant slot v (prefix over the slots' item counts)
-    int64_t cum = lane < nv ? (int64_t)ch.cpre[lane][a.n_dags] * ncb : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(FULL, cum, o);
-        if (lane >= o) cum += y;
-    }
-    cum = __shfl_up_sync(FULL, cum, 1);
-    if (lane == 0) cum = 0;
-    int32_t st = 0, nch = 0, cpre = 0, fit = 0;
-    auto meta = [&](int d) {
-        if (lane < nv) {
-            st = a.status[lane][d];
-            nch = ch.nchunk[lane][d];
-            cpre = ch.cpre[lane][d];
-            fit = a.pflag[lane][d] & 1;
-        }
-    };
-    if ((int)blockIdx.x < a.n_dags) meta(blockIdx.x);
+    int32_t st = 0;
+    if (lane < nv && (int)blockIdx.x < a.n_dags) st = a.status[lane][blockIdx.x];
     griddep_wait();
     if (blockIdx.x == 0 && lane == 0) *ch.counter = 0u;
     for (int d = blockIdx.x; d < a.n_dags; d += gridDim.x) {
-        if (d != (int)blockIdx.x) meta(d);
+        if (d != (int)blockIdx.x && lane < nv) st = a.status[lane][d];
+        unsigned long long *acc = ch.acc + (int64_t)d * n_cand;
         int64_t best_b = 0;
         int32_t best_c = -1;
-        for (int v = 0; v < nv; v++) {
-            const int st_v = __shfl_sync(FULL, st, v), nch_v = __shfl_sync(FULL, nch, v);
-            const int cpre_v = __shfl_sync(FULL, cpre, v), fit_v = __shfl_sync(FULL, fit, v);
-            const int64_t cum_v = __shfl_sync(FULL, cum, v);
-            for (int cbk = 0; cbk < ncb; cbk++) {
-                const int c = v * a.n_alloc + cbk * 64 + 2 * lane;
-                int64_t s0 = -1, s1 = -1;
-                if (st_v == DAGRT_OK) {
-                    const int64_t step = (int64_t)ncb * kPartialBytes;
-                    const unsigned char *pp = ch.partial + (cum_v + (int64_t)cpre_v * ncb + cbk) * kPartialBytes;
-                    s0 = s1 = 0;
-                    if (fit_v) {
-                        pp += 8 * lane;
-                        for (int k0 = 0; k0 < nch_v; k0 += 8) {
-                            int2 x[8];
+        for (int k0 = 0; k0 < nblk; k0 += 4) {
+            ulonglong2 x[4];
 #pragma unroll
-                            for (int k = 0; k < 8; k++)
-                                x[k] = k0 + k < nch_v ? *(const int2 *)(pp + (k0 + k) * step) : make_int2(0, 0);
+            for (int k = 0; k < 4; k++)
+                x[k] = k0 + k < nblk ? __ldcg((const ulonglong2 *)(acc + (k0 + k) * 64 + 2 * lane))
+                                     : make_ulonglong2(0, 0);
 #pragma unroll
-                            for (int k = 0; k < 8; k++) {
-                                s0 += x[k].x;
-                                s1 += x[k].y;
-                            }
-                        }
-                    } else {
-                        pp += 16 * lane;
-                        for (int k0 = 0; k0 < nch_v; k0 += 4) {
-                            longlong2 x[4];
-#pragma unroll
-                            for (int k = 0; k < 4; k++)
-                                x[k] = k0 + k < nch_v ? *(const longlong2 *)(pp + (k0 + k) * step) : make_longlong2(0, 0);
-#pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                s0 += x[k].x;
-                                s1 += x[k].y;
-                            }
-                        }
-                    }
+            for (int k = 0; k < 4; k++) {
+                if (k0 + k >= nblk) break;
+                const int c = (k0 + k) * 64 + 2 * lane;
+                const bool ok = __shfl_sync(FULL, st, (k0 + k) / ncb) == DAGRT_OK;
+                const int64_t s0 = ok ? (int64_t)x[k].x : -1, s1 = ok ? (int64_t)x[k].y : -1;
+                if (ok) {
                     better(best_b, best_c, s0, c);
                     better(best_b, best_c, s1, c + 1);
+                    *(ulonglong2 *)(acc + c) = make_ulonglong2(0, 0);
                 }
                 if (a.out) {  // the caller's buffer is only 8-byte aligned
                     a.out[(int64_t)d * n_cand + c] = s0;
@@ -569,9 +531,10 @@ __device__ __forceinline__ int high_bit(uint32_t x) {
 // the rows with table lookups; rows with other bytes take exec_time for those bytes. A
 // group of one row adds its C directly; the first row of a longer group sets its running
 // max / sum / SMs, its last row adds R_j (Lemma 1). Other items run their rows in 64-bit
-// arithmetic with exec_time for every byte. Each item writes 64 partial sums (int32 or
-// int64); k_bound_finish adds them up per candidate once every item is done. At most 64
-// registers a thread, so that eight CTAs of four warps fit an SM by registers.
+// arithmetic with exec_time for every byte. Each item adds its 64 partial sums into the
+// DAG's per-candidate 64-bit accumulators (the bound is their sum); k_bound_finish reads
+// them once every item is done. At most 64 registers a thread, so that eight CTAs of four
+// warps fit an SM by registers.
 template <bool CHECK_M>
 __global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs a, ChunkArgs ch) {
     extern __shared__ __align__(128) unsigned char sm[];
@@ -580,7 +543,7 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned char *wbase = sm + w * kWarpBytes;
     uint2 *tbuf = (uint2 *)(wbase + 2 * kStageBytes);
-    const int nv = a.n_variants, ncb = a.n_alloc / 64;
+    const int nv = a.n_variants, ncb = a.n_alloc / 64, n_cand = nv * a.n_alloc;
     const uint32_t M = (uint32_t)a.M;
     if (threadIdx.x == 0) {
         s_cum[0] = 0;
@@ -742,11 +705,10 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs
                 __syncwarp();
                 if (more) stage(buf, vi, cb, g0 + kSubRows, min(rec.z, g0 + 2 * kSubRows));
             }
-            unsigned char *slot = ch.partial + (size_t)j * kPartialBytes;
-            if constexpr (FIT)
-                *(uint2 *)(slot + 8 * lane) = make_uint2(b0, b1);
-            else
-                *(ulonglong2 *)(slot + 16 * lane) = make_ulonglong2(b0, b1);
+            // add the item's partial bounds into its DAG's accumulators (reductions: no wait)
+            unsigned long long *acc = ch.acc + (int64_t)rec.x * n_cand + vi * a.n_alloc + cb * 64 + 2 * lane;
+            atomicAdd(acc, (unsigned long long)b0);
+            atomicAdd(acc + 1, (unsigned long long)b1);
         };
         if (rec.w & 1)
             run_item(std::true_type());

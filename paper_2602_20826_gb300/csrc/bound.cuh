@@ -81,11 +81,12 @@ struct ChunkArgs {
     const int32_t *chunk[kMaxVariantsPerCall], *nchunk[kMaxVariantsPerCall], *cpre[kMaxVariantsPerCall];
     const int4 *item[kMaxVariantsPerCall];
     uint32_t *counter;            // work-item counter
-    unsigned char *partial;       // [items * 512 B]: 64 int32 partial bounds (64 int64 where sums need 64 bits)
+    unsigned long long *acc;      // [n_dags * n_cand] bound accumulators; zero between calls
     int32_t warps;                // warps per CTA of the work-item kernel
 };
 
-// scratch bytes the balanced path needs for a call (counter, partials)
+// scratch bytes the balanced path needs for a call (counter, accumulators); all of it must
+// be zero before the first call, and every call leaves it zero
 size_t bound_chunk_scratch(int32_t n_dags, int64_t total_nodes, int32_t n_variants, int32_t n_alloc, int chunk_rows);
 // the call can take the balanced path (materialised candidates, n_alloc % 64 == 0, and few
 // enough work items for 32-bit item ids)
@@ -96,8 +97,8 @@ bool bound_chunk_eligible(const BoundArgs &a, int64_t total_nodes, int chunk_row
 cudaError_t bound_selftest_wait(uint32_t limit, int32_t *word, cudaStream_t st);
 
 // Enqueue the bound kernels; *launches receives the number of kernels enqueued. With ch
-// (an eligible call), the balanced path: work items, then k_bound_finish (sums of the
-// items' partial bounds, argmin); else the tile kernels.
+// (an eligible call), the balanced path: work items adding their partial bounds into
+// per-candidate accumulators, then k_bound_finish (bounds, argmin); else the tile kernels.
 cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cudaStream_t st, int *launches);
 
 }  // namespace dagrt
