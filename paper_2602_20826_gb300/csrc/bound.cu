@@ -519,6 +519,51 @@ __device__ __forceinline__ int high_bit(uint32_t x) {
     return r;
 }
 
+// One plan row of Lemma 1's group sweep for two candidates (C, m in ta, tb): a row that
+// starts and ends its group adds C; a group's first row sets max / sum / SMs, later rows
+// accumulate, its last row adds R_j = max C if the SMs fit in M, else sum C. `start` and
+// `end` are the same in every lane, so the branches are uniform (bra.uni).
+__device__ __forceinline__ void group_step(uint32_t start, uint32_t end, uint2 ta, uint2 tb, uint32_t M,
+                                           uint32_t &gmax0, uint32_t &gmax1, uint32_t &gsum0, uint32_t &gsum1,
+                                           uint32_t &gm0, uint32_t &gm1, uint32_t &b0, uint32_t &b1) {
+    asm("{\n\t"
+        ".reg .pred ps, pe, q0, q1;\n\t"
+        ".reg .u32 t0, t1;\n\t"
+        "setp.ne.u32 ps, %8, 0;\n\t"
+        "setp.ne.u32 pe, %9, 0;\n\t"
+        "@!ps bra.uni MID;\n\t"
+        "@!pe bra.uni FIRST;\n\t"
+        "add.u32 %6, %6, %10;\n\t"
+        "add.u32 %7, %7, %12;\n\t"
+        "bra.uni DONE;\n"
+        "FIRST:\n\t"
+        "mov.u32 %0, %10;\n\t"
+        "mov.u32 %1, %12;\n\t"
+        "mov.u32 %2, %10;\n\t"
+        "mov.u32 %3, %12;\n\t"
+        "mov.u32 %4, %11;\n\t"
+        "mov.u32 %5, %13;\n\t"
+        "bra.uni DONE;\n"
+        "MID:\n\t"
+        "max.u32 %0, %0, %10;\n\t"
+        "max.u32 %1, %1, %12;\n\t"
+        "add.u32 %2, %2, %10;\n\t"
+        "add.u32 %3, %3, %12;\n\t"
+        "add.u32 %4, %4, %11;\n\t"
+        "add.u32 %5, %5, %13;\n\t"
+        "@!pe bra.uni DONE;\n\t"
+        "setp.le.u32 q0, %4, %14;\n\t"
+        "setp.le.u32 q1, %5, %14;\n\t"
+        "selp.u32 t0, %0, %2, q0;\n\t"
+        "selp.u32 t1, %1, %3, q1;\n\t"
+        "add.u32 %6, %6, t0;\n\t"
+        "add.u32 %7, %7, t1;\n"
+        "DONE:\n\t"
+        "}"
+        : "+r"(gmax0), "+r"(gmax1), "+r"(gsum0), "+r"(gsum1), "+r"(gm0), "+r"(gm1), "+r"(b0), "+r"(b1)
+        : "r"(start), "r"(end), "r"(ta.x), "r"(ta.y), "r"(tb.x), "r"(tb.y), "r"(M));
+}
+
 // Persistent warps over the work items. Per item: its rows (64 candidate bytes and the plan
 // row each, at most kSubRows per phase) are staged by cp.async -- the next item's first
 // phase is staged while this one computes.
@@ -652,28 +697,8 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs
                                 if (ma & (ma - 1)) ta = make_uint2((uint32_t)exec_time(x.x, kk, ma, M), ma);
                                 if (mb & (mb - 1)) tb = make_uint2((uint32_t)exec_time(x.x, kk, mb, M), mb);
                             }
-                            if (startm & bit) {
-                                if (endm & bit) {  // a group of one row: R = C (Lemma 1 either way)
-                                    b0 += ta.x;
-                                    b1 += tb.x;
-                                } else {
-                                    gmax0 = gsum0 = ta.x;
-                                    gmax1 = gsum1 = tb.x;
-                                    gm0 = ta.y;
-                                    gm1 = tb.y;
-                                }
-                            } else {
-                                gmax0 = max(gmax0, ta.x);
-                                gmax1 = max(gmax1, tb.x);
-                                gsum0 += ta.x;
-                                gsum1 += tb.x;
-                                gm0 += ta.y;
-                                gm1 += tb.y;
-                                if (endm & bit) {
-                                    b0 += gm0 <= M ? gmax0 : gsum0;
-                                    b1 += gm1 <= M ? gmax1 : gsum1;
-                                }
-                            }
+                            group_step(startm & bit, endm & bit, ta, tb, M, gmax0, gmax1, gsum0, gsum1, gm0, gm1,
+                                       b0, b1);
                         }
                     };
                     if (oddm)
