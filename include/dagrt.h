@@ -241,9 +241,9 @@ int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_
  *               of their class) are scheduled by warp teams in shared memory, larger ones by
  *               CTA teams with global workspaces; one of 0 (CTA teams only), 64, 128, 192,
  *               256. Default 256.
- *   chunk_rows  candidate bounds: the plan rows of a DAG are cut into work items of about
- *               this many rows at group ends (Theorem 1's sum splits there); 8 .. 256.
- *               Default 48.
+ *   chunk_rows  candidate bounds: the plan rows of a DAG are cut into work items of whole
+ *               groups (Theorem 1's sum splits at group ends), as many as fit in this many
+ *               rows (a longer group alone); 8 .. 256. Default 64.
  *   item_warps  candidate bounds: warps per CTA of the work-item kernel, 1 .. 8. Default 4.
  *   cta_smem    scheduler: k in 1 .. 4 = CTA teams keep their workspace in shared memory
  *               while it takes at most 1/k of a CTA's shared memory (smallest large DAGs
@@ -267,7 +267,7 @@ int dagrt_set_tuning(dagrt_batch *batch, const dagrt_tuning *t);
 int dagrt_autotune_schedule(dagrt_batch *batch, int32_t variant, int32_t reps, dagrt_tuning *chosen,
                             float *best_ms);
 /* Same for dagrt_bound with the given candidates (device m_alloc; every variant must have
- * been scheduled): chunk_rows in {16, 24, 32, 48} x item_warps in {2, 4, 8}. Only calls
+ * been scheduled): chunk_rows in {24, 32, 48, 64} x item_warps in {2, 4, 8}. Only calls
  * that take the work-item kernel (n_alloc a multiple of 64) have anything to tune;
  * others return the current setting unchanged. */
 int dagrt_autotune_bound(dagrt_batch *batch, int32_t n_variants, const int32_t *variant_ids,

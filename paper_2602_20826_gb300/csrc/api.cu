@@ -1360,7 +1360,7 @@ extern "C" int dagrt_autotune_bound(dagrt_batch *b, int32_t n_variants, const in
     const bool tunable = n_alloc > 0 && n_alloc % 64 == 0;
     std::vector<std::pair<int, int>> grid;
     if (tunable) {
-        for (int cr : {16, 24, 32, 48})
+        for (int cr : {24, 32, 48, 64})
             for (int wp : {2, 4, 8}) grid.emplace_back(cr, wp);
     } else {
         grid.emplace_back(b->tune.chunk_rows, b->tune.item_warps);

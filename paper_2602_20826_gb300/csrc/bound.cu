@@ -333,37 +333,36 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Chunk starts of every DAG of one plan (one warp per DAG). Chunk 0 starts at row 0; a new
-// chunk starts at the first row p >= start + chunk_rows whose previous row ends a group.
-// The group-end bits of 32 rows at a time come from one ballot; every lane walks the same
-// mask, lane 0 writes.
+// Chunk starts of every DAG of one plan (one warp per DAG). Chunk 0 starts at row 0; each
+// chunk takes whole groups, as many as fit in chunk_rows rows (at least one group), so a
+// chunk ends at the last group end within chunk_rows rows of its start, or at the end of
+// its first group if that group alone is longer. Any two neighbouring chunks hold more than
+// chunk_rows rows together. The group-end bits of 32 rows at a time come from one ballot;
+// every lane walks the same masks, lane 0 writes.
 __global__ void k_plan_chunks(int32_t n_dags, const int64_t *node_off, const uint4 *plan, const int32_t *nrows,
                               const int32_t *status, int32_t *chunk, int32_t *nchunk, int chunk_rows) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dags; d += warps) {
         const int rows = status[d] == DAGRT_OK ? nrows[d] : 0;
-        const int64_t rbase = 2 * node_off[d];
-        int count = 0, cur = 0;
-        if (rows > 0) {
-            if (lane == 0) chunk[rbase] = 0;
-            count = 1;
-        }
-        for (int base = 0; base < rows; base += 32) {
-            const int r = base + lane;
-            const bool endg = r < rows && (plan[rbase + r].z >> 24) != 0;
-            const uint32_t mask = __ballot_sync(FULL, endg);
-            for (;;) {
-                const int lo = cur + chunk_rows - 1 - base;  // bit i gives the start p = base + i + 1
-                if (lo > 31) break;
-                const uint32_t mm = lo <= 0 ? mask : (mask & (~0u << lo));
-                if (!mm) break;
-                const int p = base + __ffs(mm);
-                if (p >= rows) break;
-                if (lane == 0) chunk[rbase + count] = p;
-                count++;
-                cur = p;
+        const uint4 *pr = plan + 2 * node_off[d];
+        int count = 0;
+        for (int cur = 0; cur < rows;) {
+            if (lane == 0) chunk[2 * node_off[d] + count] = cur;
+            count++;
+            const int limit = min(rows, cur + chunk_rows);
+            int next = -1;  // one past the chunk's last row
+            for (int base = cur; base < limit; base += 32) {
+                const int r = base + lane;
+                const uint32_t mask = __ballot_sync(FULL, r < limit && (pr[r].z >> 24) != 0);
+                if (mask) next = base + 32 - __clz(mask);
             }
+            for (int base = limit; next < 0 && base < rows; base += 32) {  // a group longer than chunk_rows
+                const int r = base + lane;
+                const uint32_t mask = __ballot_sync(FULL, r < rows && (pr[r].z >> 24) != 0);
+                if (mask) next = base + __ffs(mask);
+            }
+            cur = next < 0 ? rows : next;
         }
         if (lane == 0) nchunk[d] = count;
     }

@@ -53,18 +53,17 @@ __host__ __device__ inline int gen_level(uint64_t seed, int64_t d, int64_t c, in
 
 // ---------------------------------------------------------------- balanced work items
 // For materialised candidates (n_alloc a multiple of 64), the bound is evaluated per work
-// item = (variant, DAG, chunk of ~kChunkRows plan rows cut at a group end, block of 64
+// item = (variant, DAG, chunk of whole groups of at most ~kChunkRows plan rows, block of 64
 // candidates): the bound is a sum over groups (Theorem 1), so chunks evaluate independently
 // and their partial sums add up. Chunks are a property of the plan and are built once per
 // plan.
-constexpr int kChunkRows = 48;     // default target rows per work item
+constexpr int kChunkRows = 64;     // default row limit of a work item (two staging phases)
 constexpr int kMinChunkRows = 8;
-
-// upper bound on the chunks of one plan (every chunk but a DAG's last has >= chunk_rows rows)
+// upper bound on the chunks of one plan (two neighbouring chunks hold more than chunk_rows
+// rows together)
 inline int64_t chunk_items_bound(int64_t total_nodes, int32_t n_dags, int chunk_rows) {
-    return 2 * total_nodes / chunk_rows + n_dags + 1;
+    return 2 * (2 * total_nodes / chunk_rows + 1) + n_dags + 1;
 }
-
 struct ChunkIndex {  // device arrays of one plan
     int32_t *chunk;   // [2*total_nodes]: chunk k of DAG d starts at row chunk[2*node_off[d] + k]
     int32_t *nchunk;  // [n_dags]: 0 where the DAG's schedule failed

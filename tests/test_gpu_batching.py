@@ -90,7 +90,7 @@ def test_autotuner_keeps_a_valid_setting(ctx):
         lb.schedule(v, fields=("status",))
     alloc, stride = wl.candidate_allocations(b, 4, 64, [1, 2, 4, 8, 16, 32], seed=wl.BASE_SEED + 13)
     t2, ms2 = lb.autotune_bound([0, 1, 2, 3], 64, torch.from_numpy(alloc).cuda(), stride, reps=2)
-    assert t2["chunk_rows"] in (16, 24, 32, 48) and t2["item_warps"] in (2, 4, 8) and ms2 > 0
+    assert t2["chunk_rows"] in (24, 32, 48, 64) and t2["item_warps"] in (2, 4, 8) and ms2 > 0
     ob, bb, bc = lb.bound([0, 1, 2, 3], 64, alloc, stride)
     for d in (0, 17, 59):
         r, rb, rc = oracle.search_dag(b, d, alloc, stride, 4, 64, [0, 1, 2, 3])
