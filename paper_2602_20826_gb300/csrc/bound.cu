@@ -6,14 +6,17 @@
 // the bound is a max-plus sweep along the group chain (Theorem 1): F_j = F_{j-1} + R_j,
 // with R_j = max C_i over the group if its SMs fit in M (Lemma 1), else sum C_i.
 //
-// One CTA per DAG. Row tiles of the DAG -- the candidate bytes of T rows (one contiguous
-// run of T * cand_stride bytes) and the T plan rows of every variant in the call -- stream
-// from global to shared memory with TMA bulk copies into two stages that complete on
-// mbarriers, so the loads of tile i+1 overlap the evaluation of tile i. Each thread owns
-// 1, 2 or 4 adjacent candidates of one variant (one shared load per row) and keeps their
-// running group states; the argmin over the DAG's candidates is reduced with warp
-// shuffles and shared memory in the same kernel. CTAs are as small as the candidate count
-// allows (64 threads for 256 candidates), so many DAGs are in flight per SM.
+// Two paths. Materialised candidates in blocks of 64 (n_alloc a multiple of 64) take the
+// balanced work items (k_bound_items + k_bound_finish, below): chunks of whole groups of
+// every plan, one warp per (chunk, 64-candidate block), partial bounds added into
+// per-candidate accumulators. Everything else (generated candidates, other n_alloc) takes
+// the tile kernel k_bound_tma: one CTA per DAG; row tiles of the DAG -- the candidate bytes
+// of T rows (one contiguous run of T * cand_stride bytes, or none when the candidates are
+// generated in the kernel) and the T plan rows of every variant in the call -- stream from
+// global to shared memory with TMA bulk copies into two stages that complete on mbarriers,
+// so the loads of tile i+1 overlap the evaluation of tile i. Each thread owns 1, 2 or 4
+// adjacent candidates of one variant and keeps their running group states; the argmin over
+// the DAG's candidates is reduced with warp shuffles and shared memory in the same kernel.
 #include <type_traits>
 
 #include "bound.cuh"
