@@ -128,18 +128,33 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def traffic(kernel: str, source: str):
-    """DRAM bytes per launch from the committed ncu capture, or None when the kernel's
-    source changed since the capture (profiles/traffic.json records its sha256)."""
+def traffic(kernel: str, source: str, key: str = "bytes_per_launch"):
+    """DRAM bytes (or another counter, `key`) per launch from the committed ncu capture, or
+    None when the kernel's source changed since the capture (profiles/traffic.json records
+    its sha256)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)[kernel]
         with open(os.path.join(ROOT, "paper_2602_20826_gb300", "csrc", source), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
-        return rec["bytes_per_launch"] if rec["source_sha256"] == sha else None
+        return rec[key] if rec["source_sha256"] == sha else None
     except Exception:
         return None
+
+
+def issue_roofline(warp_inst, seconds: float, clk: dict):
+    """Instruction-issue roofline of a call: its warp instructions (ncu count of the same
+    code, from profiles/traffic.json) per second against the GPU's issue peak, SMs x 4
+    schedulers x one warp instruction per cycle x the median SM clock sampled during the
+    timed region. None without a valid count or clock."""
+    import torch
+    mhz = (clk or {}).get("sm_mhz")
+    if not warp_inst or not mhz:
+        return None
+    peak = torch.cuda.get_device_properties(0).multi_processor_count * 4 * mhz * 1e6
+    return {"achieved": warp_inst / seconds, "peak": peak, "unit": "warp instructions/s",
+            "frac": warp_inst / seconds / peak, "warp_instructions_per_call": warp_inst}
 
 
 def run_cfg3_bound(args):
@@ -218,7 +233,9 @@ def run_cfg3_bound(args):
                          "frac": alg / t / 1e9 / peak, "traffic": traffic("k_bound_items", "bound.cu"),
                          "kernel": "dagrt_bound: k_bound_items + k_bound_finish (timed together; "
                                    "traffic is k_bound_items alone)",
-                         "alg_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs"}}
+                         "alg_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
+                         "issue": issue_roofline(traffic("k_bound_items", "bound.cu", "warp_instructions_per_call"),
+                                                 t, clk)}}
     print(json.dumps(line), flush=True)
 
 
