@@ -23,13 +23,25 @@ __device__ __forceinline__ uint16_t f2bf(float f) {
 }
 
 // ------------------------------------------------------------------ graph
-// One warp per DAG: global successor CSR, in-degrees, then predecessor lists filled by all
-// lanes and sorted per node (every list in increasing predecessor id: deterministic).
-__global__ void k_gnn_graph(int32_t n_dags, const int64_t *node_off, const int64_t *edge_off,
-                            const int32_t *row_ptr, const int32_t *col, const int32_t *status, int32_t *pred_off,
-                            int32_t *pred_idx, int32_t *succ_off, int32_t *succ_idx, int32_t *cursor) {
+constexpr int kGraphSmemV = 1024;  // DAGs up to this many nodes build in shared memory
+constexpr int kGraphWarps = 8;     // warps per CTA of k_gnn_graph
+constexpr int kGraphWarpInts = 2 * kGraphSmemV + 2;
+
+// One warp per DAG: global successor CSR, in-degrees, then predecessor lists with every
+// list in increasing predecessor id (deterministic). DAGs of at most kGraphSmemV nodes:
+// in-degree counts by shared-memory atomics, their exclusive scan, then a stable fill --
+// the edges in CSR order (increasing source), 32 at a time; lanes with the same target
+// rank themselves with a match, so each list comes out sorted. Larger DAGs: counts and
+// fill in global memory with atomics, then an insertion sort per list.
+__global__ void __launch_bounds__(32 * kGraphWarps)
+    k_gnn_graph(int32_t n_dags, const int64_t *node_off, const int64_t *edge_off, const int32_t *row_ptr,
+                const int32_t *col, const int32_t *status, int32_t *pred_off, int32_t *pred_idx, int32_t *succ_off,
+                int32_t *succ_idx, int32_t *cursor) {
+    extern __shared__ int32_t s_graph[];
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
+    int32_t *off = s_graph + (threadIdx.x >> 5) * kGraphWarpInts;  // [V]: counts, then next free slot
+    int32_t *rps = off + kGraphSmemV;                                // [V + 1]: the DAG's row pointers
     for (int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dags; d += warps) {
         const int64_t n0 = node_off[d], e0 = edge_off[d];
         const int V = (int)(node_off[d + 1] - n0);
@@ -46,6 +58,58 @@ __global__ void k_gnn_graph(int32_t n_dags, const int64_t *node_off, const int64
         }
         const int32_t *rp = row_ptr + n0 + d;
         const int32_t *cl = col + e0;
+        if (V <= kGraphSmemV) {
+            const int E = rp[V];
+            for (int v = lane; v <= V; v += 32) rps[v] = rp[v];
+            for (int v = lane; v < V; v += 32) {
+                off[v] = 0;
+                succ_off[n0 + v] = (int32_t)(e0 + rp[v]);
+            }
+            for (int e = lane; e < E; e += 32) succ_idx[e0 + e] = (int32_t)(n0 + cl[e]);
+            __syncwarp();
+            for (int e = lane; e < E; e += 32) atomicAdd(&off[cl[e]], 1);
+            __syncwarp();
+            int carry = 0;  // exclusive scan of the in-degrees, 32 nodes at a time
+            for (int base = 0; base < V; base += 32) {
+                const int v = base + lane;
+                const int c = v < V ? off[v] : 0;
+                int x = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (v < V) {
+                    pred_off[n0 + v] = (int32_t)(e0 + carry + x - c);
+                    off[v] = carry + x - c;
+                }
+                carry += __shfl_sync(FULL, x, 31);
+            }
+            if (lane == 0 && d == n_dags - 1) {
+                pred_off[node_off[n_dags]] = (int32_t)edge_off[n_dags];
+                succ_off[node_off[n_dags]] = (int32_t)edge_off[n_dags];
+            }
+            __syncwarp();
+            int u = 0;  // source row of the chunk's first edge
+            for (int base = 0; base < E; base += 32) {
+                const int e = base + lane;
+                const bool act = e < E;
+                const int t = act ? cl[e] : -1;
+                int r = u;
+                if (act)
+                    while (rps[r + 1] <= e) r++;
+                const uint32_t same = __match_any_sync(FULL, t);  // lanes of this chunk with target t
+                const int rank = __popc(same & ((1u << lane) - 1));
+                const int slot = act ? off[t] + rank : 0;
+                __syncwarp();
+                if (act) {
+                    if (rank == __popc(same) - 1) off[t] = slot + 1;  // the set's last lane moves the cursor
+                    pred_idx[e0 + slot] = (int32_t)(n0 + r);
+                }
+                u = __shfl_sync(FULL, r, 31);
+                __syncwarp();
+            }
+            continue;
+        }
         for (int v = lane; v < V; v += 32) {
             succ_off[n0 + v] = (int32_t)(e0 + rp[v]);
             cursor[n0 + v] = 0;
@@ -102,10 +166,13 @@ cudaError_t gnn_build_graph(int32_t n_dags, const int64_t *node_off, const int64
                             const int32_t *col, const int32_t *status, int32_t *pred_off, int32_t *pred_idx,
                             int32_t *succ_off, int32_t *succ_idx, int32_t *cursor, int n_sm, cudaStream_t st) {
     if (n_dags == 0) return cudaSuccess;
-    int grid = (n_dags + 7) / 8;
+    int grid = (n_dags + kGraphWarps - 1) / kGraphWarps;
     if (grid > 16 * n_sm) grid = 16 * n_sm;
-    k_gnn_graph<<<grid, 256, 0, st>>>(n_dags, node_off, edge_off, row_ptr, col, status, pred_off, pred_idx,
-                                      succ_off, succ_idx, cursor);
+    const int smem = kGraphWarps * kGraphWarpInts * (int)sizeof(int32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_gnn_graph, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_gnn_graph<<<grid, 32 * kGraphWarps, smem, st>>>(n_dags, node_off, edge_off, row_ptr, col, status, pred_off,
+                                                      pred_idx, succ_off, succ_idx, cursor);
     return cudaGetLastError();
 }
 
