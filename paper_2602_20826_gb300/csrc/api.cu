@@ -134,6 +134,7 @@ struct dagrt_batch {
     size_t tmp_cap = 0;
     void *bscr = nullptr;  // work-item scratch of the bound kernels
     size_t bscr_cap = 0;
+    bool bscr_dirty = false;  // a call failed part way: clear the counters and accumulators first
     // learned proposer: message-passing graph, features, activations (allocated on first use)
     struct Gnn {
         bool graph = false, train = false;
@@ -528,7 +529,13 @@ static int ensure_chunks(dagrt_batch *b, int variant) {
 
 static int ensure_bscr(dagrt_batch *b, size_t bytes) {
     dagrt_ctx *ctx = b->ctx;
-    if (b->bscr_cap >= bytes) return DAGRT_OK;
+    if (b->bscr_cap >= bytes && !b->bscr_dirty) return DAGRT_OK;
+    if (b->bscr_cap >= bytes) {
+        if (ctx->capturing) return fail(ctx, DAGRT_E_INVAL, "bound scratch must be cleared outside graph capture");
+        CK(cudaMemsetAsync(b->bscr, 0, b->bscr_cap, ctx->stream), "clear bound scratch");
+        b->bscr_dirty = false;
+        return DAGRT_OK;
+    }
     if (ctx->capturing) return fail(ctx, DAGRT_E_INVAL, "scratch must grow during graph capture: make the call once before capturing");
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     if (b->bscr) ctx->pool.put(b->bscr, b->bscr_cap);
@@ -540,6 +547,7 @@ static int ensure_bscr(dagrt_batch *b, size_t bytes) {
     // the work-item counter and the bound accumulators start at zero; every call leaves
     // them zero
     CK(cudaMemsetAsync(b->bscr, 0, bytes, ctx->stream), "clear bound scratch");
+    b->bscr_dirty = false;
     return DAGRT_OK;
 }
 
@@ -783,7 +791,13 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
         ch.warps = b->tune.item_warps;
     }
     int nl = 0;
-    CK(bound_launch(a, items ? &ch : nullptr, ctx->n_sm, ctx->stream, &nl), "launch bound kernel");
+    {
+        const cudaError_t e = bound_launch(a, items ? &ch : nullptr, ctx->n_sm, ctx->stream, &nl);
+        if (e != cudaSuccess) {
+            if (items) b->bscr_dirty = true;  // the work items may have run without the finish
+            return cuda_fail(ctx, e, "launch bound kernel");
+        }
+    }
     ctx->launches += nl;
     if (dev) return DAGRT_OK;
     if (out_bound && out_bytes) CK(cudaMemcpyAsync(out_bound, a.out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy bounds");
