@@ -665,9 +665,8 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     }
     tm.sync();
 
-    // ---- in-degrees (a join has at least two predecessors)
-    for (int u = tm.t; u < V; u += NT)
-        for (int e = rp[u]; e < rp[u + 1]; e++) atomicAdd(&ws.cnt[col[e]], 1);
+    // ---- in-degrees (a join has at least two predecessors), one edge per thread
+    for (int e = tm.t; e < (int)E; e += NT) atomicAdd(&ws.cnt[col[e]], 1);
     const int W = (V + 63) >> 6;
     for (int i = tm.t; i < V * W; i += NT) ws.anc[i] = 0;
     if (lead) sc[0] = 0;
@@ -873,9 +872,23 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         bigblk = tm.any(bigblk);
         tm.sync();
     }
-    for (int u = tm.t; u < V; u += NT)
-        for (int e = rp[u]; e < rp[u + 1]; e++)
-            if (ws.blk[col[e]] == ws.blk[u]) atomicAdd(&ws.cnt[col[e]], 1);
+    if constexpr (NT == 32) {
+        // in-block parents, one edge per lane: the edges are in CSR order, so a lane finds its
+        // source row a few rows after the row of the round's first edge
+        for (int e0 = 0, u0 = 0; e0 < (int)E; e0 += 32) {
+            const int e = e0 + tm.t;
+            int u = u0;
+            if (e < (int)E) {
+                while ((int)rp[u + 1] <= e) u++;
+                if (ws.blk[col[e]] == ws.blk[u]) atomicAdd(&ws.cnt[col[e]], 1);
+            }
+            u0 = __shfl_sync(FULL, u, 31);  // lane 31 holds the latest row (or u0 past the end)
+        }
+    } else {
+        for (int u = tm.t; u < V; u += NT)
+            for (int e = rp[u]; e < rp[u + 1]; e++)
+                if (ws.blk[col[e]] == ws.blk[u]) atomicAdd(&ws.cnt[col[e]], 1);
+    }
     tm.sync();
     bad = false;
     for (int v = tm.t; v < V; v += NT) {
