@@ -688,23 +688,24 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     int ls = 0, le = sc[0], L = 0;
     if (lead) ws.lvl_off[0] = 0;
     while (ls < le) {
-        if constexpr (NT == 32) {
-            // a warp team spreads the level's out-edges over its lanes: up to 32 nodes at a
-            // time, each lane finding the owner of its edge by a binary search over the
-            // nodes' edge offsets (an exclusive scan of their out-degrees)
-            for (int base = ls; base < le; base += 32) {
-                const int i = base + tm.t;
+        {
+            // every warp spreads the out-edges of a slice of up to 32 of the level's nodes over
+            // its lanes, each lane finding the owner of its edge by a binary search over the
+            // slice's edge offsets (an exclusive scan of their out-degrees)
+            const int ln = tm.lane();
+            for (int base = ls + 32 * tm.warp(); base < le; base += NT) {
+                const int i = base + ln;
                 const int u = i < le ? ws.topo[i] : 0;
                 const int eb = i < le ? (int)rp[u] : 0;
                 const int deg = i < le ? (int)rp[u + 1] - eb : 0;
                 int x = deg;
                 for (int o = 1; o < 32; o <<= 1) {
                     const int y = __shfl_up_sync(FULL, x, o);
-                    if (tm.t >= o) x += y;
+                    if (ln >= o) x += y;
                 }
                 const int start = x - deg, total = __shfl_sync(FULL, x, 31);
                 for (int f0 = 0; f0 < total; f0 += 32) {
-                    const int f = f0 + tm.t;
+                    const int f = f0 + ln;
                     int j = 0;  // the last node whose edges start at or before f
                     for (int step = 16; step; step >>= 1) {
                         const int sj = __shfl_sync(FULL, start, j + step);
@@ -727,29 +728,10 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
                     }
                     const uint32_t rm = __ballot_sync(FULL, rel);
                     int p0 = 0;
-                    if (tm.t == 0 && rm) p0 = atomicAdd((int *)&sc[0], __popc(rm));
+                    if (ln == 0 && rm) p0 = atomicAdd((int *)&sc[0], __popc(rm));
                     p0 = __shfl_sync(FULL, p0, 0);
                     if (rel) {
-                        ws.topo[p0 + __popc(rm & ((1u << tm.t) - 1))] = (uint16_t)s;
-                        if (a.o.level) a.o.level[n0 + s] = L + 1;
-                    }
-                }
-            }
-        } else {
-            for (int i = ls + tm.t; i < le; i += NT) {
-                const int u = ws.topo[i];
-                const uint64_t *au = ws.anc + (int64_t)u * W;
-                for (int e = rp[u]; e < rp[u + 1]; e++) {
-                    const int s = col[e];
-                    unsigned long long *as = (unsigned long long *)(ws.anc + (int64_t)s * W);
-                    for (int w = 0; w < W; w++) {
-                        const uint64_t x = au[w];
-                        if (x) atomicOr(&as[w], (unsigned long long)x);
-                    }
-                    atomicOr(&as[u >> 6], 1ull << (u & 63));
-                    if (atomicSub(&ws.cnt[s], 1) == 1) {
-                        const int p = atomicAdd((int *)&sc[0], 1);
-                        ws.topo[p] = (uint16_t)s;
+                        ws.topo[p0 + __popc(rm & ((1u << ln) - 1))] = (uint16_t)s;
                         if (a.o.level) a.o.level[n0 + s] = L + 1;
                     }
                 }
