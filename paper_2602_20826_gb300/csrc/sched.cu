@@ -688,52 +688,50 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     int ls = 0, le = sc[0], L = 0;
     if (lead) ws.lvl_off[0] = 0;
     while (ls < le) {
-        {
-            // every warp spreads the out-edges of a slice of up to 32 of the level's nodes over
-            // its lanes, each lane finding the owner of its edge by a binary search over the
-            // slice's edge offsets (an exclusive scan of their out-degrees)
-            const int ln = tm.lane();
-            for (int base = ls + 32 * tm.warp(); base < le; base += NT) {
-                const int i = base + ln;
-                const int u = i < le ? ws.topo[i] : 0;
-                const int eb = i < le ? (int)rp[u] : 0;
-                const int deg = i < le ? (int)rp[u + 1] - eb : 0;
-                int x = deg;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(FULL, x, o);
-                    if (ln >= o) x += y;
+        // every warp spreads the out-edges of a slice of up to 32 of the level's nodes over
+        // its lanes, each lane finding the owner of its edge by a binary search over the
+        // slice's edge offsets (an exclusive scan of their out-degrees)
+        const int ln = tm.lane();
+        for (int base = ls + 32 * tm.warp(); base < le; base += NT) {
+            const int i = base + ln;
+            const int u = i < le ? ws.topo[i] : 0;
+            const int eb = i < le ? (int)rp[u] : 0;
+            const int deg = i < le ? (int)rp[u + 1] - eb : 0;
+            int x = deg;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (ln >= o) x += y;
+            }
+            const int start = x - deg, total = __shfl_sync(FULL, x, 31);
+            for (int f0 = 0; f0 < total; f0 += 32) {
+                const int f = f0 + ln;
+                int j = 0;  // the last node whose edges start at or before f
+                for (int step = 16; step; step >>= 1) {
+                    const int sj = __shfl_sync(FULL, start, j + step);
+                    if (sj <= f) j += step;
                 }
-                const int start = x - deg, total = __shfl_sync(FULL, x, 31);
-                for (int f0 = 0; f0 < total; f0 += 32) {
-                    const int f = f0 + ln;
-                    int j = 0;  // the last node whose edges start at or before f
-                    for (int step = 16; step; step >>= 1) {
-                        const int sj = __shfl_sync(FULL, start, j + step);
-                        if (sj <= f) j += step;
+                const int uo = __shfl_sync(FULL, u, j), eo = __shfl_sync(FULL, eb, j);
+                const int so = __shfl_sync(FULL, start, j);
+                bool rel = false;
+                int s = 0;
+                if (f < total) {
+                    s = col[eo + f - so];
+                    const uint64_t *au = ws.anc + (int64_t)uo * W;
+                    unsigned long long *as = (unsigned long long *)(ws.anc + (int64_t)s * W);
+                    for (int w = 0; w < W; w++) {
+                        const uint64_t y = au[w];
+                        if (y) atomicOr(&as[w], (unsigned long long)y);
                     }
-                    const int uo = __shfl_sync(FULL, u, j), eo = __shfl_sync(FULL, eb, j);
-                    const int so = __shfl_sync(FULL, start, j);
-                    bool rel = false;
-                    int s = 0;
-                    if (f < total) {
-                        s = col[eo + f - so];
-                        const uint64_t *au = ws.anc + (int64_t)uo * W;
-                        unsigned long long *as = (unsigned long long *)(ws.anc + (int64_t)s * W);
-                        for (int w = 0; w < W; w++) {
-                            const uint64_t y = au[w];
-                            if (y) atomicOr(&as[w], (unsigned long long)y);
-                        }
-                        atomicOr(&as[uo >> 6], 1ull << (uo & 63));
-                        rel = atomicSub(&ws.cnt[s], 1) == 1;
-                    }
-                    const uint32_t rm = __ballot_sync(FULL, rel);
-                    int p0 = 0;
-                    if (ln == 0 && rm) p0 = atomicAdd((int *)&sc[0], __popc(rm));
-                    p0 = __shfl_sync(FULL, p0, 0);
-                    if (rel) {
-                        ws.topo[p0 + __popc(rm & ((1u << ln) - 1))] = (uint16_t)s;
-                        if (a.o.level) a.o.level[n0 + s] = L + 1;
-                    }
+                    atomicOr(&as[uo >> 6], 1ull << (uo & 63));
+                    rel = atomicSub(&ws.cnt[s], 1) == 1;
+                }
+                const uint32_t rm = __ballot_sync(FULL, rel);
+                int p0 = 0;
+                if (ln == 0 && rm) p0 = atomicAdd((int *)&sc[0], __popc(rm));
+                p0 = __shfl_sync(FULL, p0, 0);
+                if (rel) {
+                    ws.topo[p0 + __popc(rm & ((1u << ln) - 1))] = (uint16_t)s;
+                    if (a.o.level) a.o.level[n0 + s] = L + 1;
                 }
             }
         }
