@@ -55,6 +55,7 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="bounded CPU work of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-cfg3", action="store_true", help="skip the config-3 candidate-bound keys")
     return p.parse_args()
 
 
@@ -157,19 +158,19 @@ def issue_roofline(warp_inst, seconds: float, clk: dict):
             "frac": warp_inst / seconds / peak, "warp_instructions_per_call": warp_inst}
 
 
-def run_cfg3_bound(args):
+def measure_cfg3_bound(args, ctx):
     """Candidate bounds of config 3: 1,000 DAGs x (4 variants x 64 allocations from
-    {1,...,32}, allocation 0 = the schedule's own), materialised in HBM, argmin per DAG."""
+    {1,...,32}, allocation 0 = the schedule's own), materialised in HBM, argmin per DAG.
+    One dagrt_bound call per step, CUDA events on the launching stream, L2 flushed between
+    steps; e2e repeats the call with host buffers. Returns the measurement record."""
     import torch
     from paper_2602_20826_gb300 import workloads as wl
-    from paper_2602_20826_gb300.dagrt import Context
-    torch.cuda.set_device(0)
     b = wl.config(3)
     stream = torch.cuda.current_stream()
-    ctx = Context(0, stream.cuda_stream)
     lb = ctx.load(b)
+    rows = 0
     for v in range(4):
-        lb.schedule(v, fields=("status",))
+        rows += int(lb.schedule(v, fields=("n_rows",))["n_rows"].sum())
     alloc, stride = wl.candidate_allocations(b, 4, 64, [1, 2, 4, 8, 16, 32], seed=wl.BASE_SEED + 13)
     da = torch.from_numpy(alloc).cuda()
     nd, nc = b.n_dags, 256
@@ -177,6 +178,7 @@ def run_cfg3_bound(args):
     bb = torch.zeros(nd, dtype=torch.int64, device="cuda")
     bc = torch.zeros(nd, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    steps = max(args.steps, 3)
     # the timed steps take well under a millisecond: the clock sampler (100 ms period)
     # runs from a half-second warm-up through the timed region
     clocks = ClockSampler(torch.cuda.current_device())
@@ -188,7 +190,7 @@ def run_cfg3_bound(args):
             torch.cuda.synchronize()
         w += 1
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     l0 = ctx.launches()
     for e0, e1 in evs:
         flush.zero_()
@@ -196,46 +198,63 @@ def run_cfg3_bound(args):
         lb.bound([0, 1, 2, 3], 64, da, stride, ob, bb, bc)
         e1.record(stream)
     torch.cuda.synchronize()
-    launches = (ctx.launches() - l0) // args.steps
+    launches = (ctx.launches() - l0) // steps
     clk = clocks.stop()
-    t = sum(a.elapsed_time(c) for a, c in evs) / 1e3 / args.steps
+    t = sum(a.elapsed_time(c) for a, c in evs) / 1e3 / steps
+    gpu_best = bb.cpu().numpy()
     # end to end: the candidate bytes from pinned host memory, every bound and the argmin
     # back to host memory, through the same C call with host pointers
     ha = torch.from_numpy(alloc).pin_memory().numpy()
     for _ in range(2):
         lb.bound([0, 1, 2, 3], 64, ha, stride)
     t_e2e = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hob, hbb, hbc = lb.bound([0, 1, 2, 3], 64, ha, stride)
         t_e2e.append(time.perf_counter() - t0)
-    assert np.array_equal(hbb, bb.cpu().numpy()) and np.array_equal(hbc, bc.cpu().numpy())
+    ok = np.array_equal(hbb, gpu_best) and np.array_equal(hbc, bc.cpu().numpy())
     te = float(np.median(t_e2e))
-    # algorithmic bytes: every plan row of every variant once (16 B) with its 64 candidate
-    # bytes of that variant, one int64 bound per candidate, best bound + candidate per DAG
+    lb.free()
+    # algorithmic bytes: each variant's candidate bytes of its plan rows once (64 B a row),
+    # the DAG data once, one int64 bound per candidate and the argmin per DAG
     peak, kind = _peaks()
-    rows = 0
-    for v in range(4):
-        rows += int(lb.schedule(v, fields=("n_rows",))["n_rows"].sum())
-    alg = rows * (64 + 16) + nd * nc * 8 + nd * 12
-    line = {"metric": "exact candidate-bound evals/s", "value": nd * nc / t, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
-            "dtype": "int64", "data": "synthetic",
+    alg = rows * 64 + b.input_bytes() + nd * nc * 8 + nd * 12
+    return {"b": b, "alloc": alloc, "stride": stride, "gpu_best": gpu_best, "ok": ok,
+            "rec": {"value": nd * nc / t, "unit": UNIT, "us_per_call": 1e6 * t, "steps": steps,
+                    "gpu_launches": launches, "clocks": clk,
+                    "e2e": {"value": nd * nc / te, "unit": UNIT, "h2d_bytes_per_step": int(alloc.nbytes),
+                            "d2h_bytes_per_step": nd * nc * 8 + nd * 12},
+                    "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": peak, "unit": "GB/s",
+                                 "frac": alg / t / 1e9 / peak, "traffic": traffic("k_bound_items", "bound.cu"),
+                                 "kernel": "dagrt_bound: k_bound_items + k_bound_finish (timed together; "
+                                           "traffic is k_bound_items alone)",
+                                 "alg_bytes_per_launch": alg,
+                                 "alg_bytes": "64 B of candidate bytes per plan row of each variant "
+                                              f"({rows} rows) + DAG data once + 8 B per candidate + 12 B per DAG",
+                                 "peak_source": f"{kind} hbm_gbs",
+                                 "issue": issue_roofline(traffic("k_bound_items", "bound.cu",
+                                                                 "warp_instructions_per_call"), t, clk)}}}
+
+
+def run_cfg3_bound(args):
+    import torch
+    from paper_2602_20826_gb300.dagrt import Context
+    torch.cuda.set_device(0)
+    ctx = Context(0, torch.cuda.current_stream().cuda_stream)
+    m = measure_cfg3_bound(args, ctx)
+    r = m["rec"]
+    nd = m["b"].n_dags
+    line = {"metric": "exact candidate-bound evals/s", "value": r["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": r["steps"], "warmup": args.warmup, "ms_per_step": r["us_per_call"] / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
             "config": {"workload": "config 3: 1,000 ER DAGs 50-500 nodes p=0.05, M=148, 4 variants x 64 "
                                    "allocations from {1..32} materialised in HBM, argmin per DAG",
-                       "l2": "flushed between steps (256 MB write)"},
-            "gpu_launches": launches, "clocks": clk,
-            "e2e": {"value": nd * nc / te, "unit": UNIT, "h2d_bytes_per_step": int(alloc.nbytes),
-                    "d2h_bytes_per_step": nd * nc * 8 + nd * 12},
-            "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": alg / t / 1e9 / peak, "traffic": traffic("k_bound_items", "bound.cu"),
-                         "kernel": "dagrt_bound: k_bound_items + k_bound_finish (timed together; "
-                                   "traffic is k_bound_items alone)",
-                         "alg_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
-                         "issue": issue_roofline(traffic("k_bound_items", "bound.cu", "warp_instructions_per_call"),
-                                                 t, clk)}}
+                       "n_dags": nd, "l2": "flushed between steps (256 MB write)"},
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "e2e": r["e2e"],
+            "roofline": r["roofline"], "status_ok": m["ok"]}
     print(json.dumps(line), flush=True)
 
 
@@ -439,58 +458,113 @@ def run_cfg5(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(batch, seconds: float, gpu_bounds=None):
-    """The oracle as it stands, single-threaded on this host, over whole passes of the DAGs
-    in order until about `seconds` of CPU time; also checks the GPU bounds of every DAG it
-    ran."""
-    import numpy as np
+def oracle_rate(batch, seconds: float, threads: int, gpu_bounds=None, chunk: int = 64):
+    """DAG schedules + bounds per second of the oracle as it stands, over whole passes of the
+    batch's DAGs in order for about `seconds`, with `threads` host threads taking chunks of
+    DAGs in turn (the oracle's C call releases the GIL and reads the batch in place). Checks
+    the GPU bounds of every DAG it ran in its first pass."""
+    import threading
     import oracle
     n = batch.n_dags
-    done, t0 = 0, time.perf_counter()
-    chunk = 500
-    mism = 0
-    checked = 0
-    while True:
-        lo = done % n
-        ids = list(range(lo, min(lo + chunk, n)))
-        bo, st = oracle.schedule_batch(batch, dags=ids)
-        if gpu_bounds is not None and checked < n:
-            mism += int(np.sum(bo != gpu_bounds[ids]))
-            checked += len(ids)
-        done += len(ids)
-        if time.perf_counter() - t0 >= seconds and done >= chunk:
-            break
+    lock = threading.Lock()
+    st = {"next": 0, "done": 0, "mism": 0, "checked": 0}
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with lock:
+                if st["next"] >= chunk * threads and time.perf_counter() - t0 >= seconds:
+                    return
+                lo = st["next"] % n
+                hi = min(lo + chunk, n)
+                first = st["next"] < n
+                st["next"] += hi - lo
+            bo, _ = oracle.schedule_range(batch, lo, hi)
+            with lock:
+                st["done"] += hi - lo
+                if gpu_bounds is not None and first:
+                    st["mism"] += int(np.sum(bo != gpu_bounds[lo:hi]))
+                    st["checked"] += hi - lo
+
+    ts = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} DAG schedules+bounds of the same batch (passes over its DAGs in "
-                      f"order), single-threaded plain-C oracle, {dt:.1f} s",
-            "parity_checked_dags": checked, "parity_mismatches": mism}
+    return {"value": st["done"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{st['done']} DAG schedules+bounds of the same batch (passes over its DAGs in "
+                      f"order), plain-C oracle, {threads} host thread(s), {dt:.1f} s",
+            "parity_checked_dags": st["checked"], "parity_mismatches": st["mism"]}
+
+
+def cpu_baseline(batch, seconds: float, gpu_bounds=None):
+    """The oracle on every host core (one thread per core, os.cpu_count()), with the
+    single-thread rate beside it; each leg takes about half of `seconds`."""
+    one = oracle_rate(batch, seconds / 2, 1, gpu_bounds)
+    allc = oracle_rate(batch, seconds / 2, os.cpu_count() or 1, gpu_bounds)
+    allc["single_thread"] = {k: one[k] for k in ("value", "cores", "sample")}
+    allc["parity_checked_dags"] = max(one["parity_checked_dags"], allc["parity_checked_dags"])
+    allc["parity_mismatches"] = one["parity_mismatches"] + allc["parity_mismatches"]
+    return allc
+
+
+def oracle_pass(batch, lo: int, hi: int, threads: int, chunk: int = 64):
+    """The oracle on DAGs lo..hi-1 of the batch, `threads` host threads taking chunks of
+    DAGs in turn; returns the bounds."""
+    import threading
+    import oracle
+    out = np.zeros(hi - lo, np.int64)
+    lock = threading.Lock()
+    nxt = [lo]
+
+    def worker():
+        while True:
+            with lock:
+                a = nxt[0]
+                nxt[0] = min(hi, a + chunk)
+            if a >= hi:
+                return
+            b = min(hi, a + chunk)
+            out[a - lo:b - lo] = oracle.schedule_range(batch, a, b)[0]
+
+    ts = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return out
 
 
 def run_reference(args, rank, world):
+    """The oracle (the paper ships no code) on the host cores of rank 0, one thread per
+    core, each step a bounded sample of the same batch."""
     from paper_2602_20826_gb300 import workloads as wl
     if rank != 0:
         return
     batch = wl.config(2)
     import oracle
-    per_step = 1000  # DAGs per step: ~0.2 s of oracle work
-    ids = list(range(per_step))
+    oracle.lib()
+    cores = os.cpu_count() or 1
+    per_step = min(batch.n_dags, 250 * cores)  # DAGs per step: ~0.3 s of oracle work per core
     for _ in range(args.warmup):
-        oracle.schedule_batch(batch, dags=ids)
+        oracle_pass(batch, 0, min(per_step, 64 * cores), cores)
     t0 = time.perf_counter()
     for s in range(args.steps):
         lo = (s * per_step) % batch.n_dags
-        oracle.schedule_batch(batch, dags=list(range(lo, lo + per_step)))
+        oracle_pass(batch, lo, min(batch.n_dags, lo + per_step), cores)
     dt = time.perf_counter() - t0
-    val = per_step * args.steps / dt
+    done = sum(min(batch.n_dags, (s * per_step) % batch.n_dags + per_step) - (s * per_step) % batch.n_dags
+               for s in range(args.steps))
+    val = done / dt
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_dags": batch.n_dags, "M": batch.M,
-                       "reference_step": f"{per_step} DAGs of the batch per step"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} DAGs per step x {args.steps} steps, single-threaded"},
+                       "reference_step": f"{per_step} DAGs of the batch per step on {cores} host threads"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} DAGs per step x {args.steps} steps, one thread per host core"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -658,8 +732,22 @@ def main():
         "clocks": clk,
         "status_ok": ok,
     }
+    line["roofline"]["issue"] = issue_roofline(traffic("k_sched_warp", "sched.cu", "warp_instructions_per_call"),
+                                               t_kern / args.steps, clk)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, args.cpu_seconds, gpu_bounds)
+    if rank == 0 and world == 1 and not args.no_cfg3:
+        # the candidate-bound kernel on config 3, the HBM-roofline part of the path
+        m = measure_cfg3_bound(args, ctx)
+        import oracle
+        b3 = m["b"]
+        for d in range(0, b3.n_dags, b3.n_dags // 8):
+            _, rb, _ = oracle.search_dag(b3, d, m["alloc"], m["stride"], 4, 64)
+            m["ok"] = m["ok"] and int(m["gpu_best"][d]) == rb
+        line["cfg3_bound"] = dict(m["rec"], status_ok=m["ok"],
+                                  workload="config 3: 1,000 ER DAGs 50-500 nodes p=0.05, M=148; 4 variants x 64 "
+                                           "allocations from {1..32} materialised in HBM (256k exact bounds), "
+                                           "argmin per DAG; parity: 8 sampled DAGs against the oracle")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -209,30 +209,35 @@ int dagrt_search(dagrt_batch *batch, const dagrt_search_cfg *cfg, int64_t *out_b
 
 /* Scheduler entry point for callers that cannot allocate device memory at run time:
  * real-time executives that reserve every buffer before their task set starts (an
- * allocation may block for an unbounded time), work recorded into CUDA graphs or run under
- * a memory budget owned by someone else, and plug-ins whose host framework forbids
- * cudaMalloc. The paper has no counterpart; it is an operational variant of
- * dagrt_load_csr + dagrt_schedule(variant) that keeps only each DAG's bound and status.
+ * allocation may block for an unbounded time), work run under a memory budget owned by
+ * someone else, and plug-ins whose host framework forbids cudaMalloc. The paper has no
+ * counterpart; it is an operational variant of dagrt_load_csr + dagrt_schedule(variant)
+ * that keeps only each DAG's bound and status.
  *
  * It allocates nothing: the scheduler's scratch (the per-team workspaces of the large-DAG
  * kernel and its work counter) lives in one fixed 4 MiB __device__ array inside the
  * library, which every GPU that loads the library holds until the process exits. All
- * array arguments are device pointers with dagrt_load_csr's layout; bound[n_dags] and
- * status[n_dags] receive dagrt_schedule's values. DAGs of more than 512 nodes or 8192 edges
- * (or with negative node/edge counts) are rejected with status DAGRT_E_INVAL and bound -1.
+ * array arguments are device pointers with dagrt_load_csr's layout; total_nodes and
+ * total_edges are the lengths of wcet/k64 (row_ptr holds total_nodes + n_dags entries) and
+ * of col. The offsets are not read on the host: the kernel checks each DAG against those
+ * lengths and gives a DAG whose node or edge range reaches outside them (or has a negative
+ * count) status DAGRT_E_INVAL and bound -1, as it does for DAGs of more than 512 nodes or
+ * 8192 edges. bound[n_dags] and status[n_dags] receive dagrt_schedule's values otherwise.
  * The call only enqueues work on `cuda_stream` (a cudaStream_t, NULL = legacy default);
  * results are valid once the caller synchronises that stream.
  *
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before capturing any stream into a graph. Every call shares the
- * array and resets its counter, so calls whose kernels overlap on the GPU (two streams,
- * two host threads) race and give wrong results: order them.
- * Returns DAGRT_OK, DAGRT_E_INVAL (NULL pointer, n_dags < 0, M or variant out of range) or
- * DAGRT_E_DEVICE (a CUDA call failed). */
+ * Every call looks up the array's device address (cudaGetSymbolAddress) with the caller's
+ * current device, so a device reset between calls is harmless; the first call on a device
+ * also loads the library's device code, so make it before capturing any stream. Every call
+ * shares the array and resets its counter, so calls whose kernels overlap on the GPU (two
+ * streams, two host threads) race and give wrong results: order them.
+ * Returns DAGRT_OK, DAGRT_E_INVAL (a NULL pointer -- col may be NULL only when total_edges
+ * is 0 --, n_dags or a length < 0, M or variant out of range) or DAGRT_E_DEVICE (a CUDA
+ * call failed). */
 int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_t *edge_off,
                            const int32_t *row_ptr, const int32_t *col, const int64_t *wcet,
-                           const uint8_t *k64, int32_t M, int32_t variant, int64_t *bound,
-                           int32_t *status, void *cuda_stream);
+                           const uint8_t *k64, int64_t total_nodes, int64_t total_edges, int32_t M,
+                           int32_t variant, int64_t *bound, int32_t *status, void *cuda_stream);
 
 /* ---------------------------------------------------------------- batching controls
  * Launch-shape choices of the batched kernels. None of them changes a result: every

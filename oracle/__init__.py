@@ -170,6 +170,26 @@ def schedule_batch(batch, variant: int = VAR_PAPER, dags=None):
     return bound, status
 
 
+def _at(a, off, t):
+    """Pointer to element `off` of numpy array `a` (no copy)."""
+    return C.cast(a.ctypes.data + int(off) * a.itemsize, t)
+
+
+def schedule_range(batch, lo: int, hi: int, variant: int = VAR_PAPER):
+    """Paper-schedule bound of DAGs lo..hi-1 of the batch, read in place (no copy, so that
+    host threads can run disjoint ranges at once): (bound, status)."""
+    n = hi - lo
+    bound = np.zeros(max(n, 1), np.int64)
+    status = np.zeros(max(n, 1), np.int32)
+    col = batch.col if len(batch.col) else np.zeros(1, np.int32)
+    # DAG lo + i reads row_ptr[node_off[lo + i] + lo + i]: shift the row_ptr base by lo
+    lib().or_schedule_batch(n, _at(batch.node_off, lo, _P64), _at(batch.edge_off, lo, _P64),
+                            _at(batch.row_ptr, lo, _P32), _ptr(col, _P32), _ptr(batch.wcet, _P64),
+                            _ptr(batch.k64, _PU8), int(batch.M), int(variant), _ptr(bound, _P64),
+                            _ptr(status, _P32))
+    return bound[:n], status[:n]
+
+
 def schedule_dag_of(batch, d: int, variant: int = VAR_PAPER, extra_cap: int = 0):
     rp, col, w, k = batch.dag(d)
     return schedule(rp, col, w, k, batch.M, variant, extra_cap)

@@ -177,6 +177,43 @@ def loss_and_grad(p, x, preds, succs, labels, n_levels, bf=True):
     return loss, pack(G)
 
 
+def grad_magnitude(p, x, preds, succs, labels, n_levels, bf=True):
+    """Element-wise scale of the rounding error of the gradient: the backward pass of
+    loss_and_grad run on absolute values (|dz|, |h|, |A|, |W| in place of the signed terms,
+    the same ReLU gates), so every gradient element's sum of |products| -- the quantity a
+    relative rounding error of each product (bf16 operands, fp32 sums) is proportional to,
+    carried through the layers as the backward pass carries the gradient. By the triangle
+    inequality it bounds |gradient| element-wise."""
+    P = unpack(p)
+    logits, cache = forward(p, x, preds, succs, n_levels, bf)
+    lab = np.asarray(labels)
+    mask = (lab >= 0) & (lab < n_levels)
+    n = int(mask.sum())
+    G = {name: np.zeros(shape) for name, shape in _SIZES}
+    if n == 0:
+        return pack(G)
+    z = logits - logits.max(axis=1, keepdims=True)
+    lse = np.log(np.exp(z).sum(axis=1))
+    dz = np.exp(z - lse[:, None])
+    dz[np.arange(len(lab)), np.where(mask, lab, 0)] -= 1.0
+    dz[~mask] = 0.0
+    dz = np.abs(dz) / n
+    h3 = cache[2][3]
+    G["Wh"][:, :n_levels] = np.abs(h3).T @ dz
+    G["bh"][:n_levels] = dz.sum(axis=0)
+    dh = dz @ np.abs(P["Wh"][:, :n_levels]).T
+    for l in (2, 1, 0):
+        h_in, A, zl, _ = cache[l]
+        W = P[f"W{l + 1}"]
+        dZ = dh * (zl > 0)
+        G[f"W{l + 1}"] = np.abs(A).T @ dZ
+        G[f"b{l + 1}"] = dZ.sum(axis=0)
+        if l > 0:
+            Wr = bf16(W) if bf else W
+            dh = aggregate_T(dZ @ np.abs(Wr).T, preds, succs, h_in.shape[1])
+    return pack(G)
+
+
 def adam(p, m, v, g, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam step (bias-corrected moments); returns new (p, m, v)."""
     m = b1 * m + (1 - b1) * g

@@ -1,5 +1,5 @@
 /*
- * oracle.c -- plain, slow, single-threaded CPU oracle for the makespan bound of
+ * oracle.c -- plain, slow CPU oracle (one thread per DAG) for the makespan bound of
  * "Exploiting Dependency and Parallelism: Real-Time Scheduling and Analysis for GPU
  * Tasks" (DAC '26).
  *
@@ -109,8 +109,9 @@ int64_t or_exec_time(int64_t load, int64_t k, int64_t m, int64_t M)
 static int bit_get(const uint64_t *set, int64_t i) { return (int)((set[i >> 6] >> (i & 63)) & 1u); }
 static void bit_set(uint64_t *set, int64_t i) { set[i >> 6] |= (uint64_t)1 << (i & 63); }
 
-/* ordering keys used with qsort */
-static const int64_t *g_key_w;
+/* the sort key of the comparators below; one per thread, so that threads may schedule
+ * different DAGs at once (the all-cores timing of the oracle) */
+static _Thread_local const int64_t *g_key_w;
 static int cmp_w_asc_id_asc(const void *a, const void *b)
 {
     int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;

@@ -646,6 +646,8 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
     a.status = p.status;
     a.bound = p.bound;
     a.oversize_status = DAGRT_E_INTERNAL;  // the size classes guarantee every DAG fits
+    a.tot_nodes = -1;                       // offsets checked by dagrt_load_csr
+    a.tot_edges = -1;
     a.nrows = p.nrows;
     a.pflag = p.pflag;
     a.plan = p.rows;

@@ -596,7 +596,9 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     volatile int32_t *sc = ws.sc;
     const bool lead = tm.t == 0;
 
-    if (V < 0 || E < 0 || V > vc || E > ec) {  // does not fit this workspace
+    // does not fit this workspace, or its offsets reach outside the arrays
+    if (V < 0 || E < 0 || V > vc || E > ec ||
+        (a.tot_nodes >= 0 && (n0 < 0 || n0 + V > a.tot_nodes || e0 < 0 || e0 + E > a.tot_edges))) {
         if (lead) write_failure(a, d, a.oversize_status);
         return;
     }

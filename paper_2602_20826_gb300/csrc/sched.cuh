@@ -32,6 +32,10 @@ struct SchedArgs {
     int64_t *bound;
     // status of a DAG larger than the workspace (or with negative offsets)
     int32_t oversize_status;
+    // lengths of the node arrays (wcet, k64; row_ptr holds tot_nodes + n_dags entries) and
+    // of col: a DAG whose offsets reach outside them gets oversize_status; -1 = not checked
+    // (the offsets were checked on the host)
+    int64_t tot_nodes, tot_edges;
     // plan of the schedule (NULL: not kept): row count, flags, rows at 2*node_off[d]
     int32_t *nrows;
     int32_t *pflag;      // per DAG: bit 0 = candidate bounds of this DAG fit 32-bit sums

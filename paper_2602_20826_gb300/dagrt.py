@@ -66,7 +66,8 @@ class dagrt_search_cfg(C.Structure):
 
 dagrt_search = _sig("dagrt_search", C.c_int, [_vp, C.POINTER(dagrt_search_cfg), _vp, _vp, _vp, _vp, C.c_uint32])
 dagrt_schedule_noalloc = _sig("dagrt_schedule_noalloc", C.c_int,
-                              [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp])
+                              [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int64, C.c_int32,
+                               C.c_int32, _vp, _vp, _vp])
 
 dagrt_model_n_params = _sig("dagrt_model_n_params", C.c_int64, [])
 dagrt_model_create = _sig("dagrt_model_create", C.c_int, [_vp, C.c_int32, _vp, C.c_uint64, C.POINTER(_vp)])
@@ -351,14 +352,38 @@ class LoadedBatch:
                 "best_bound": bb[:self.n_dags], "best_cand": bc[:self.n_dags], "best_m": bm}
 
 
+_BATCH_DTYPES = {"node_off": "int64", "edge_off": "int64", "row_ptr": "int32", "col": "int32",
+                 "wcet": "int64", "k64": "uint8"}
+
+
+def _check_device_array(name, t, dtype, min_len):
+    """A contiguous torch CUDA tensor of `dtype` with at least min_len elements."""
+    if t is None or not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name}: a torch CUDA tensor is required")
+    if str(t.dtype) != f"torch.{dtype}":
+        raise ValueError(f"{name}: dtype {t.dtype}, expected torch.{dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.numel() < min_len:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {min_len} needed")
+
+
 def schedule_noalloc(dev: dict, M: int, variant: int, bound, status, stream=None) -> int:
     """dagrt_schedule_noalloc on a batch held in torch CUDA tensors (keys as for
-    Context.load); bound and status are torch CUDA tensors of n_dags entries. Enqueues
-    only; returns the C status code."""
+    Context.load); bound (int64) and status (int32) are torch CUDA tensors of n_dags
+    entries. The array lengths passed to the library are the tensors' own lengths, so the
+    kernel rejects offsets that reach outside them. Enqueues only; returns the C status."""
     n = int(dev["node_off"].shape[0]) - 1
+    for k, dt in _BATCH_DTYPES.items():
+        _check_device_array(k, dev[k], dt, 0)
+    _check_device_array("bound", bound, "int64", n)
+    _check_device_array("status", status, "int32", n)
+    tot_nodes = min(int(dev["wcet"].numel()), int(dev["k64"].numel()), int(dev["row_ptr"].numel()) - max(n, 0))
+    tot_edges = int(dev["col"].numel())
     return int(dagrt_schedule_noalloc(n, _ptr(dev["node_off"]), _ptr(dev["edge_off"]), _ptr(dev["row_ptr"]),
-                                      _ptr(dev["col"]), _ptr(dev["wcet"]), _ptr(dev["k64"]), int(M),
-                                      int(variant), _ptr(bound), _ptr(status), stream))
+                                      _ptr(dev["col"]) if tot_edges else None, _ptr(dev["wcet"]), _ptr(dev["k64"]),
+                                      max(tot_nodes, 0), tot_edges, int(M), int(variant), _ptr(bound),
+                                      _ptr(status), stream))
 
 
 class Model:

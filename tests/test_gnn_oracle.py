@@ -126,6 +126,41 @@ def test_gradient_central_differences():
     assert np.all(g[a:e].reshape(G.HIDDEN, G.MAX_LEVELS)[:, L:] == 0)
 
 
+def test_grad_magnitude_bounds_gradient_and_is_exact_without_cancellation():
+    """grad_magnitude (the error scale of the GPU gradient test) is the backward pass on
+    absolute values: it bounds |gradient| element-wise, and equals it where no term can
+    cancel -- all parameters and inputs non-negative and one labelled node whose softmax
+    gradient is zero except on its label (a one-level head)."""
+    b, preds, succs, x, p, rng = _tiny(5, n_dags=2)
+    L = 6
+    labels = rng.integers(-1, L, size=b.total_nodes())
+    _, g = G.loss_and_grad(p, x, preds, succs, labels, L, bf=False)
+    mag = G.grad_magnitude(p, x, preds, succs, labels, L, bf=False)
+    assert (np.abs(g) <= mag * (1 + 1e-12) + 1e-300).all()
+    assert mag.max() > 0
+    # no cancellation: non-negative inputs and weights, two levels whose head column 0 is
+    # zero, so dh = p_1 * Wh[:, 1] >= 0 and every product below the head is >= 0
+    pa = np.abs(p) * 0.05
+    P = G.unpack(pa)
+    P["Wh"][:, 0] = 0.0
+    P["bh"][:] = 0.0
+    xa = np.abs(x)
+    lab = np.full(b.total_nodes(), -1)
+    lab[:3] = 0
+    _, g1 = G.loss_and_grad(pa, xa, preds, succs, lab, 2, bf=False)
+    m1 = G.grad_magnitude(pa, xa, preds, succs, lab, 2, bf=False)
+    blocks = {}
+    o = 0
+    for name, shape in G._SIZES:
+        n = int(np.prod(shape))
+        blocks[name] = (o, o + n)
+        o += n
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        a, e = blocks[name]
+        assert m1[a:e].max() > 0, name
+        assert np.allclose(np.abs(g1[a:e]), m1[a:e], rtol=1e-10, atol=1e-300), name
+
+
 def test_cross_entropy_closed_form_at_zero_head():
     b, preds, succs, x, p, rng = _tiny(4)
     P = G.unpack(p)

@@ -180,6 +180,30 @@ def test_config5_layered_sampled(ctx):
         assert res["n_rows"][d] == V + res["n_seg"][d]
 
 
+@pytest.mark.slow
+def test_config5_full_batch_three_largest_in_full(ctx):
+    """The whole 200-DAG layered batch in the benchmark's launch configuration (CTA teams,
+    global workspaces sized for the largest DAG); the three largest DAGs (about 20,000
+    nodes each: the largest closures, released-set masks and Top_M ballots) are compared
+    with the oracle in every output, their extra edges in a second run of just those three,
+    and every DAG's bound against properties that hold at any size."""
+    b = wl.config(5)
+    lb, res = gpu_schedule(ctx, b, 0, edges=False)
+    sizes = np.diff(b.node_off)
+    big = [int(d) for d in np.argsort(sizes)[-3:]]
+    assert min(sizes[big]) > 19000
+    for d in big:
+        compare_dag(b, res, d, 0, edges=False)
+    for d in range(b.n_dags):
+        n0, V, G = int(b.node_off[d]), int(sizes[d]), res["n_groups"][d]
+        assert res["status"][d] == 0
+        assert res["bound"][d] == res["group_R"][n0:n0 + G].sum()
+        assert res["bound"][d] >= -(-int(b.wcet[n0:n0 + V].sum()) // b.M)
+        assert res["n_rows"][d] == V + res["n_seg"][d]
+    lb.free()
+    _check_batch(ctx, b.subset(big), 0, edges=True)
+
+
 @pytest.mark.parametrize("variant", [0, 3])
 def test_mid_size_dags_mask_summary_and_top_m(ctx, variant):
     """DAGs of 600-1,500 nodes: released-set masks of 10-24 words (walked through their
