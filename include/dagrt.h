@@ -186,11 +186,25 @@ int dagrt_bound(dagrt_batch *batch, int32_t n_variants, const int32_t *variant_i
 /* Schedule search over generated candidate allocations (the problem formulation of Sec.
  * 2.2: choose m_i and the DAG structure to minimise the bound). Candidate c =
  * v * n_alloc + a of DAG d runs on the plan of structure variant variant_ids[v] (each must
- * have been scheduled on the batch); allocation a = 0 keeps the schedule's own m, and for
- * a > 0 plan row r gets levels[i] with i drawn by a counter-based generator: x = seed +
- * (d << 40 | c << 20 | r), z = SplitMix64(x) (Steele, Lea and Flood, OOPSLA 2014),
- * i = ((z >> 32) * n_levels) >> 32. Every candidate's bound is exact (as dagrt_bound).
- * Limits: n_variants * n_alloc <= 2^20, n_levels in [1, 16], levels in [1, 255]. */
+ * have been scheduled on the batch); allocation a = 0 keeps the schedule's own m in every
+ * mode. Every candidate's bound is exact (as dagrt_bound). Modes:
+ *  DAGRT_SEARCH_RANDOM: for a > 0, plan row r gets levels[i] with i drawn by a
+ *    counter-based generator: x = seed + (d << 40 | c << 20 | r), z = SplitMix64(x)
+ *    (Steele, Lea and Flood, OOPSLA 2014), i = ((z >> 32) * n_levels) >> 32.
+ *  DAGRT_SEARCH_EXHAUSTIVE: allocation a is a number in base B = n_levels + 1 whose digit
+ *    u, (a / B^u) % B, sets the SMs of node u (on every plan row of u, its segments
+ *    included): digit 0 keeps the schedule's m, digit i > 0 gives levels[i-1]. With
+ *    n_alloc = B^V every allocation in ({schedule's m} + levels)^V of a V-node DAG is
+ *    evaluated once; nodes with B^u > a keep the schedule's m. (seed is unused.)
+ *  DAGRT_SEARCH_PERTURB: for a > 0, plan row r gets a change of its scheduled SMs m0,
+ *    levels[i] (i drawn as in RANDOM) naming it: 0 keep, 1 halve (at least 1), 2 one fewer
+ *    (at least 1), 3 one more, 4 double; changed counts are capped at 255. Repeating code 0
+ *    in levels makes sparse perturbations of the schedule's own (Eq.5) allocation.
+ * Limits: n_variants * n_alloc <= 2^20, n_levels in [1, 16] (at most 15 in EXHAUSTIVE),
+ * levels in [1, 255] (codes in [0, 4] in PERTURB). */
+#define DAGRT_SEARCH_RANDOM 0
+#define DAGRT_SEARCH_EXHAUSTIVE 1
+#define DAGRT_SEARCH_PERTURB 2
 typedef struct {
     int32_t n_variants;
     const int32_t *variant_ids;  /* host array */
@@ -198,6 +212,7 @@ typedef struct {
     int32_t n_levels;
     const uint8_t *levels;       /* host array */
     uint64_t seed;
+    int32_t mode;                /* DAGRT_SEARCH_* */
 } dagrt_search_cfg;
 
 /* out_bound [n_dags * n_cand] (may be NULL); best_bound, best_cand [n_dags] as in

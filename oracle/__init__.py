@@ -66,6 +66,9 @@ def lib():
         _lib.or_splitmix64.argtypes = [C.c_uint64]
         _lib.or_gen_level.restype = C.c_int32
         _lib.or_gen_level.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, C.c_int32]
+        _lib.or_exhaustive_plan.restype = None
+        _lib.or_exhaustive_plan.argtypes = [C.c_int32, _P64, _P32, _P32, _P32, _P32, C.c_int32, C.c_int32, _PU8,
+                                            C.c_int64, _P64]
         _lib.or_schedule_batch.restype = C.c_int64
         _lib.or_schedule_batch.argtypes = [C.c_int32, _P64, _P64, _P32, _P32, _P64, _PU8, C.c_int32,
                                            C.c_int32, _P64, _P32]
@@ -235,7 +238,86 @@ def generated_allocation(seed: int, d: int, c: int, n_rows: int, levels, n_alloc
     return out
 
 
-def search_dag_generated(batch, d: int, variant_ids, n_alloc: int, levels, seed: int):
+SEARCH_RANDOM, SEARCH_EXHAUSTIVE, SEARCH_PERTURB = 0, 1, 2
+
+
+def row_owner(plan: dict) -> np.ndarray:
+    """Node each plan row belongs to: the row's node, or a segment's parent."""
+    V = int(plan["V"])
+    out = [int(r) if r < V else int(plan["seg_parent"][r - V]) for r in plan["row_id"][:plan["n_rows"]]]
+    return np.asarray(out, np.int32)
+
+
+def exhaustive_plan(plan: dict, M: int, levels, n_alloc: int) -> np.ndarray:
+    """Bounds of allocations 0..n_alloc-1 of the exhaustive search on one plan (see
+    or_exhaustive_plan): node u's digit (a / B^u) % B, B = len(levels) + 1, keeps (0) or
+    picks levels[digit - 1] on every plan row of u."""
+    n = int(plan["n_rows"])
+    out = np.zeros(max(n_alloc, 1), np.int64)
+    lev = np.ascontiguousarray(levels, np.uint8)
+    own = np.ascontiguousarray(row_owner(plan) if n else np.zeros(1, np.int32), np.int32)
+    load = np.ascontiguousarray(plan["row_load"] if n else np.zeros(1, np.int64), np.int64)
+    k = np.ascontiguousarray(plan["row_k"] if n else np.zeros(1, np.int32), np.int32)
+    m0 = np.ascontiguousarray(plan["row_m0"] if n else np.zeros(1, np.int32), np.int32)
+    g = np.ascontiguousarray(plan["row_group"] if n else np.zeros(1, np.int32), np.int32)
+    lib().or_exhaustive_plan(n, _ptr(load, _P64), _ptr(k, _P32), _ptr(m0, _P32), _ptr(g, _P32), _ptr(own, _P32),
+                             int(M), len(lev), _ptr(lev, _PU8), int(n_alloc), _ptr(out, _P64))
+    return out[:n_alloc]
+
+
+def exhaustive_search_dag(batch, d: int, variant_ids, levels, n_alloc: int):
+    """Bounds of every candidate c = v * n_alloc + a of the exhaustive search of DAG d and
+    the argmin (smallest bound, lowest candidate id)."""
+    out = np.zeros(len(variant_ids) * n_alloc, np.int64)
+    for vi, var in enumerate(variant_ids):
+        rc, plan = schedule_dag_of(batch, d, int(var))
+        if rc != OK:
+            raise RuntimeError(f"oracle schedule failed: {rc}")
+        out[vi * n_alloc:(vi + 1) * n_alloc] = exhaustive_plan(plan, batch.M, levels, n_alloc)
+    best = int(np.argmin(out))
+    return out, int(out[best]), best
+
+
+def perturbed_m(m0: int, code: int) -> int:
+    """SMs of a row scheduled on m0 SMs under perturbation `code`: 0 keeps the schedule
+    (returned as 0), 1 halves, 2 takes one away, 3 adds one, 4 doubles; a changed count is
+    at least 1 and at most 255."""
+    if code == 0:
+        return 0
+    m = {1: m0 // 2, 2: m0 - 1, 3: m0 + 1, 4: 2 * m0}[code]
+    return min(255, max(1, m))
+
+
+def search_dag_generated(batch, d: int, variant_ids, n_alloc: int, levels, seed: int, mode: int = SEARCH_RANDOM):
+    """Bounds of every generated candidate of DAG d and the argmin (min bound, lowest id)
+    for the random, exhaustive or perturbation search."""
+    if mode == SEARCH_EXHAUSTIVE:
+        return exhaustive_search_dag(batch, d, variant_ids, levels, n_alloc)
+    if mode == SEARCH_PERTURB:
+        plans = {}
+        out = np.zeros(len(variant_ids) * n_alloc, np.int64)
+        L = lib()
+        for vi, var in enumerate(variant_ids):
+            if var not in plans:
+                rc, plans[var] = schedule_dag_of(batch, d, int(var))
+                if rc != OK:
+                    raise RuntimeError(f"oracle schedule failed: {rc}")
+            plan = plans[var]
+            n = int(plan["n_rows"])
+            for a in range(n_alloc):
+                c = vi * n_alloc + a
+                alloc = np.zeros(max(n, 1), np.uint8)[:n]
+                if a:
+                    for r in range(n):
+                        code = int(levels[L.or_gen_level(C.c_uint64(seed), d, c, r, len(levels))])
+                        alloc[r] = perturbed_m(int(plan["row_m0"][r]), code)
+                out[c] = bound_plan(plan, batch.M, alloc if n else None, 1)
+        best = int(np.argmin(out))
+        return out, int(out[best]), best
+    return search_dag_random(batch, d, variant_ids, n_alloc, levels, seed)
+
+
+def search_dag_random(batch, d: int, variant_ids, n_alloc: int, levels, seed: int):
     """Bounds of every generated candidate of DAG d and the argmin (min bound, lowest id)."""
     plans = {}
     nv = len(variant_ids)

@@ -177,21 +177,32 @@ def loss_and_grad(p, x, preds, succs, labels, n_levels, bf=True):
     return loss, pack(G)
 
 
-def grad_magnitude(p, x, preds, succs, labels, n_levels, bf=True):
-    """Element-wise scale of the rounding error of the gradient: the backward pass of
-    loss_and_grad run on absolute values (|dz|, |h|, |A|, |W| in place of the signed terms,
-    the same ReLU gates), so every gradient element's sum of |products| -- the quantity a
-    relative rounding error of each product (bf16 operands, fp32 sums) is proportional to,
-    carried through the layers as the backward pass carries the gradient. By the triangle
-    inequality it bounds |gradient| element-wise."""
+def grad_magnitude(p, x, preds, succs, labels, n_levels, bf=True, gate_slack=0.0):
+    """Element-wise scales of the difference between this gradient and one computed with
+    other rounding (bf16 operands, fp32 sums), as a pair (mag, flip):
+
+    mag -- the backward pass of loss_and_grad run on absolute values (|dz|, |h|, |A|, |W|
+    in place of the signed terms): every gradient element's sum of |products|, the quantity
+    a relative rounding error of each product is proportional to, carried through the
+    layers as the backward pass carries the gradient. By the triangle inequality it bounds
+    |gradient| element-wise.
+
+    flip -- a bound on what ReLU gates that rounding may set the other way can change: a
+    gate is uncertain where |z| is within gate_slack of the sum |A| |W| + |b| that z adds
+    up. An uncertain gate adds or drops its whole term |dh| at its layer, and that change
+    flows down through the later (lower) layers on absolute values with every open or
+    uncertain gate passing it.
+
+    gate_slack = 0 gives exactly the gates of loss_and_grad (flip = 0)."""
     P = unpack(p)
     logits, cache = forward(p, x, preds, succs, n_levels, bf)
     lab = np.asarray(labels)
     mask = (lab >= 0) & (lab < n_levels)
     n = int(mask.sum())
     G = {name: np.zeros(shape) for name, shape in _SIZES}
+    F = {name: np.zeros(shape) for name, shape in _SIZES}
     if n == 0:
-        return pack(G)
+        return pack(G), pack(F)
     z = logits - logits.max(axis=1, keepdims=True)
     lse = np.log(np.exp(z).sum(axis=1))
     dz = np.exp(z - lse[:, None])
@@ -202,16 +213,24 @@ def grad_magnitude(p, x, preds, succs, labels, n_levels, bf=True):
     G["Wh"][:, :n_levels] = np.abs(h3).T @ dz
     G["bh"][:n_levels] = dz.sum(axis=0)
     dh = dz @ np.abs(P["Wh"][:, :n_levels]).T
+    eh = np.zeros_like(dh)  # bound on the change of dh that flipped gates above can cause
     for l in (2, 1, 0):
         h_in, A, zl, _ = cache[l]
         W = P[f"W{l + 1}"]
-        dZ = dh * (zl > 0)
+        Wr = bf16(W) if bf else W
+        zmag = np.abs(A) @ np.abs(Wr) + np.abs(P[f"b{l + 1}"])
+        unsure = np.abs(zl) <= gate_slack * zmag
+        gate = (zl > 0) | unsure
+        dZ = dh * gate
+        eZ = eh * gate + dh * unsure
         G[f"W{l + 1}"] = np.abs(A).T @ dZ
         G[f"b{l + 1}"] = dZ.sum(axis=0)
+        F[f"W{l + 1}"] = np.abs(A).T @ eZ
+        F[f"b{l + 1}"] = eZ.sum(axis=0)
         if l > 0:
-            Wr = bf16(W) if bf else W
             dh = aggregate_T(dZ @ np.abs(Wr).T, preds, succs, h_in.shape[1])
-    return pack(G)
+            eh = aggregate_T(eZ @ np.abs(Wr).T, preds, succs, h_in.shape[1])
+    return pack(G), pack(F)
 
 
 def adam(p, m, v, g, step, lr, b1=0.9, b2=0.999, eps=1e-8):

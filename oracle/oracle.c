@@ -598,3 +598,29 @@ int32_t or_gen_level(uint64_t seed, int64_t d, int64_t c, int64_t r, int32_t n_l
     uint64_t hi = or_splitmix64(x) >> 32;
     return (int32_t)((hi * (uint64_t)n_levels) >> 32);
 }
+
+/* ------------------------------------------------- exhaustive allocation search */
+
+/* Every allocation of a fixed schedule structure in which each node u gets either the
+ * schedule's own SMs or one of n_levels levels, on all of its plan rows: allocation a is
+ * read as a number in base B = n_levels + 1 whose digit u, (a / B^u) % B, is 0 (keep) or
+ * i (levels[i-1]). row_owner[r] is the node plan row r belongs to (a segment's parent).
+ * out[a] receives the bound of allocation a, for a in [0, n_alloc). */
+void or_exhaustive_plan(int32_t n_rows, const int64_t *row_load, const int32_t *row_k,
+                        const int32_t *row_m0, const int32_t *row_group, const int32_t *row_owner,
+                        int32_t M, int32_t n_levels, const uint8_t *levels, int64_t n_alloc,
+                        int64_t *out)
+{
+    int64_t B = n_levels + 1;
+    uint8_t *alloc = malloc((size_t)(n_rows > 0 ? n_rows : 1));
+    for (int64_t a = 0; a < n_alloc; a++) {
+        for (int32_t r = 0; r < n_rows; r++) {
+            int64_t q = a;
+            for (int32_t u = 0; u < row_owner[r]; u++) q /= B;
+            int64_t digit = q % B;
+            alloc[r] = digit == 0 ? 0 : levels[digit - 1];
+        }
+        out[a] = or_bound_plan(n_rows, row_load, row_k, row_m0, row_group, M, alloc, 1);
+    }
+    free(alloc);
+}

@@ -825,10 +825,18 @@ extern "C" int dagrt_search(dagrt_batch *b, const dagrt_search_cfg *cfg, int64_t
         return fail(ctx, DAGRT_E_INVAL, "dagrt_search: n_variants must be in [1, %d]", kMaxVariantsPerCall);
     if (cfg->n_alloc < 1 || (int64_t)cfg->n_variants * cfg->n_alloc > (1 << 20))
         return fail(ctx, DAGRT_E_INVAL, "dagrt_search: need 1 <= n_alloc and n_variants * n_alloc <= 2^20");
-    if (cfg->n_levels < 1 || cfg->n_levels > 16 || !cfg->levels)
-        return fail(ctx, DAGRT_E_INVAL, "dagrt_search: n_levels must be in [1, 16]");
-    for (int i = 0; i < cfg->n_levels; i++)
-        if (cfg->levels[i] < 1) return fail(ctx, DAGRT_E_INVAL, "dagrt_search: level %d is 0", i);
+    const int mode = cfg->mode;
+    if (mode != DAGRT_SEARCH_RANDOM && mode != DAGRT_SEARCH_EXHAUSTIVE && mode != DAGRT_SEARCH_PERTURB)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_search: unknown mode %d", mode);
+    const int max_levels = mode == DAGRT_SEARCH_EXHAUSTIVE ? 15 : 16;
+    if (cfg->n_levels < 1 || cfg->n_levels > max_levels || !cfg->levels)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_search: n_levels must be in [1, %d]", max_levels);
+    for (int i = 0; i < cfg->n_levels; i++) {
+        if (mode != DAGRT_SEARCH_PERTURB && cfg->levels[i] < 1)
+            return fail(ctx, DAGRT_E_INVAL, "dagrt_search: level %d is 0", i);
+        if (mode == DAGRT_SEARCH_PERTURB && cfg->levels[i] > 4)
+            return fail(ctx, DAGRT_E_INVAL, "dagrt_search: perturbation code %d is not in [0, 4]", i);
+    }
     if (b->n_dags >= (1 << 24)) return fail(ctx, DAGRT_E_INVAL, "dagrt_search: too many DAGs");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     BoundArgs a;
@@ -841,6 +849,7 @@ extern "C" int dagrt_search(dagrt_batch *b, const dagrt_search_cfg *cfg, int64_t
     a.stride = 16;
     a.err = b->err;
     a.gen = 1;
+    a.gen_mode = mode;
     a.seed = cfg->seed;
     a.n_levels = cfg->n_levels;
     for (int i = 0; i < 16; i++) a.levels[i] = i < cfg->n_levels ? cfg->levels[i] : cfg->levels[0];

@@ -109,18 +109,31 @@ __host__ __device__ inline TileLayout tile_layout(int T, int64_t stride, int nv)
     return t;
 }
 
+// SMs of plan row `row` (owner node `owner`, scheduled on m0 SMs) for generated candidate c
+// of DAG d; 0 keeps the schedule's m.
+__device__ __forceinline__ uint32_t gen_alloc(const BoundArgs &a, int d, int c, int row, uint32_t owner, uint32_t m0,
+                                              const uint8_t *s_lev) {
+    const int al = c % a.n_alloc;
+    if (a.gen_mode == DAGRT_SEARCH_EXHAUSTIVE) {
+        const uint32_t dg = exh_digit((uint32_t)al, owner, (uint32_t)a.n_levels + 1u);
+        return dg ? s_lev[dg - 1] : 0u;
+    }
+    if (al == 0) return 0u;
+    const uint32_t x = s_lev[gen_level(a.seed, d, c, row, a.n_levels)];
+    if (a.gen_mode != DAGRT_SEARCH_PERTURB) return x;
+    return x == 0 ? 0u : perturb_m(m0, x);  // code 0 keeps the row's own m (even above 255)
+}
+
 // Candidate bytes of one row for a thread's CPT adjacent candidates (one shared load), or
-// the generated levels of those candidates.
+// the generated allocations of those candidates.
 template <int CPT, bool GEN>
 __device__ __forceinline__ uint32_t row_alloc(const BoundArgs &a, const unsigned char *cbuf, int64_t stride, int rr,
-                                              int d, int c, int row, const uint8_t *s_lev) {
+                                              int d, int c, int row, uint32_t owner, uint32_t m0,
+                                              const uint8_t *s_lev) {
     if (GEN) {
         uint32_t m4 = 0;
 #pragma unroll
-        for (int q = 0; q < CPT; q++) {
-            const int cq = c + q;
-            if (cq % a.n_alloc != 0) m4 |= (uint32_t)s_lev[gen_level(a.seed, d, cq, row, a.n_levels)] << (8 * q);
-        }
+        for (int q = 0; q < CPT; q++) m4 |= gen_alloc(a, d, c + q, row, owner, m0, s_lev) << (8 * q);
         return m4;
     }
     if (CPT == 4) return *(const uint32_t *)(cbuf + rr * stride);
@@ -182,7 +195,7 @@ __device__ __forceinline__ bool eval_tiles(const BoundArgs &a, int d, int c, int
             const uint4 x = pl[rr];
             const uint32_t k = (x.z >> 16) & 0xffu, m0 = x.z & 0xffffu;
             const bool last = (x.z >> 24) != 0;
-            const uint32_t m4 = row_alloc<CPT, GEN>(a, cbuf, stride, rr, d, c, r0 + rr, s_lev);
+            const uint32_t m4 = row_alloc<CPT, GEN>(a, cbuf, stride, rr, d, c, r0 + rr, x.w, m0, s_lev);
             S cc[CPT];
             if (FIT) {
                 const uint32_t A1 = x.x * (64u - k) + 64u, B1 = x.x * k - 1u;
@@ -309,8 +322,10 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
             if (GEN && a.best_m && s_bc[0] >= 0) {  // the winning allocation, row by row
                 const int wc = s_bc[0], wv = wc / a.n_alloc;
                 const int rows = a.nrows[wv][d];
-                for (int r = tid; r < rows; r += blockDim.x)
-                    a.best_m[rbase + r] = wc % a.n_alloc == 0 ? 0 : s_lev[gen_level(a.seed, d, wc, r, a.n_levels)];
+                for (int r = tid; r < rows; r += blockDim.x) {
+                    const uint4 x = a.plan[wv][rbase + r];
+                    a.best_m[rbase + r] = (uint8_t)gen_alloc(a, d, wc, r, x.w, x.z & 0xffffu, s_lev);
+                }
             }
             __syncthreads();
         }

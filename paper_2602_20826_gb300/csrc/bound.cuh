@@ -31,6 +31,7 @@ struct BoundArgs {
     // generated candidates (dagrt_search): m of row r of candidate c = v*n_alloc + a is
     // levels[gen_level(seed, d, c, r)] for a > 0 and the scheduled m for a == 0
     int32_t gen;
+    int32_t gen_mode;                           // DAGRT_SEARCH_RANDOM / _EXHAUSTIVE / _PERTURB
     uint64_t seed;
     int32_t n_levels;
     uint8_t levels[16];
@@ -49,6 +50,18 @@ __host__ __device__ inline uint64_t splitmix64(uint64_t x) {
 __host__ __device__ inline int gen_level(uint64_t seed, int64_t d, int64_t c, int64_t r, int n_levels) {
     const uint64_t x = seed + (((uint64_t)d << 40) | ((uint64_t)c << 20) | (uint64_t)r);
     return (int)(((splitmix64(x) >> 32) * (uint64_t)n_levels) >> 32);
+}
+
+// Digit of node u in allocation a written in base B (exhaustive search): (a / B^u) % B.
+__host__ __device__ inline uint32_t exh_digit(uint32_t a, uint32_t u, uint32_t B) {
+    for (; u > 0 && a; u--) a /= B;
+    return a % B;
+}
+// SMs of a plan row scheduled on m0 SMs after perturbation `code` (perturbation search):
+// 0 keep, 1 halve, 2 one fewer, 3 one more, 4 double; at least 1, at most 255.
+__host__ __device__ inline uint32_t perturb_m(uint32_t m0, uint32_t code) {
+    uint32_t m = code == 1 ? m0 / 2 : code == 2 ? m0 - 1 : code == 3 ? m0 + 1 : code == 4 ? 2 * m0 : m0;
+    return m < 1 ? 1u : (m > 255 ? 255u : m);
 }
 
 // ---------------------------------------------------------------- balanced work items

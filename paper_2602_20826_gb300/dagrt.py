@@ -59,9 +59,13 @@ dagrt_batch_total_nodes = _sig("dagrt_batch_total_nodes", C.c_int64, [_vp])
 dagrt_schedule = _sig("dagrt_schedule", C.c_int, [_vp, C.c_int32, C.POINTER(dagrt_schedule_out), C.c_uint32])
 dagrt_bound = _sig("dagrt_bound", C.c_int,
                    [_vp, C.c_int32, C.POINTER(C.c_int32), C.c_int32, _vp, C.c_int64, _vp, _vp, _vp, C.c_uint32])
+SEARCH_RANDOM, SEARCH_EXHAUSTIVE, SEARCH_PERTURB = 0, 1, 2
+
+
 class dagrt_search_cfg(C.Structure):
     _fields_ = [("n_variants", C.c_int32), ("variant_ids", C.POINTER(C.c_int32)), ("n_alloc", C.c_int32),
-                ("n_levels", C.c_int32), ("levels", C.POINTER(C.c_uint8)), ("seed", C.c_uint64)]
+                ("n_levels", C.c_int32), ("levels", C.POINTER(C.c_uint8)), ("seed", C.c_uint64),
+                ("mode", C.c_int32)]
 
 
 dagrt_search = _sig("dagrt_search", C.c_int, [_vp, C.POINTER(dagrt_search_cfg), _vp, _vp, _vp, _vp, C.c_uint32])
@@ -328,14 +332,16 @@ class LoadedBatch:
         return (ob[:self.n_dags * n_cand].reshape(self.n_dags, n_cand) if want_all else None,
                 bb[:self.n_dags], bc[:self.n_dags])
 
-    def search(self, variant_ids, n_alloc: int, levels, seed: int, want_all: bool = False,
-               want_m: bool = False, out=None):
-        """dagrt_search over generated candidates. Host outputs (numpy) by default; with
-        `out` (dict of torch CUDA tensors: out_bound/best_bound/best_cand/best_m, any
-        subset) the call only enqueues device work."""
+    def search(self, variant_ids, n_alloc: int, levels, seed: int = 0, want_all: bool = False,
+               want_m: bool = False, out=None, mode: int = SEARCH_RANDOM):
+        """dagrt_search over generated candidates (mode: SEARCH_RANDOM, SEARCH_EXHAUSTIVE or
+        SEARCH_PERTURB). Host outputs (numpy) by default; with `out` (dict of torch CUDA
+        tensors: out_bound/best_bound/best_cand/best_m, any subset) the call only enqueues
+        device work."""
         vids = (C.c_int32 * len(variant_ids))(*[int(v) for v in variant_ids])
         lev = (C.c_uint8 * len(levels))(*[int(x) for x in levels])
-        cfg = dagrt_search_cfg(len(variant_ids), vids, int(n_alloc), len(levels), lev, C.c_uint64(seed & (2**64 - 1)))
+        cfg = dagrt_search_cfg(len(variant_ids), vids, int(n_alloc), len(levels), lev, C.c_uint64(seed & (2**64 - 1)),
+                               int(mode))
         if out is not None:
             rc = dagrt_search(self.h, C.byref(cfg), _ptr(out.get("out_bound")), _ptr(out.get("best_bound")),
                               _ptr(out.get("best_cand")), _ptr(out.get("best_m")), PTR_DEVICE)

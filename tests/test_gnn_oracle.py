@@ -135,7 +135,8 @@ def test_grad_magnitude_bounds_gradient_and_is_exact_without_cancellation():
     L = 6
     labels = rng.integers(-1, L, size=b.total_nodes())
     _, g = G.loss_and_grad(p, x, preds, succs, labels, L, bf=False)
-    mag = G.grad_magnitude(p, x, preds, succs, labels, L, bf=False)
+    mag, flip = G.grad_magnitude(p, x, preds, succs, labels, L, bf=False)
+    assert not flip.any()
     assert (np.abs(g) <= mag * (1 + 1e-12) + 1e-300).all()
     assert mag.max() > 0
     # no cancellation: non-negative inputs and weights, two levels whose head column 0 is
@@ -148,7 +149,7 @@ def test_grad_magnitude_bounds_gradient_and_is_exact_without_cancellation():
     lab = np.full(b.total_nodes(), -1)
     lab[:3] = 0
     _, g1 = G.loss_and_grad(pa, xa, preds, succs, lab, 2, bf=False)
-    m1 = G.grad_magnitude(pa, xa, preds, succs, lab, 2, bf=False)
+    m1, _ = G.grad_magnitude(pa, xa, preds, succs, lab, 2, bf=False)
     blocks = {}
     o = 0
     for name, shape in G._SIZES:
@@ -159,6 +160,57 @@ def test_grad_magnitude_bounds_gradient_and_is_exact_without_cancellation():
         a, e = blocks[name]
         assert m1[a:e].max() > 0, name
         assert np.allclose(np.abs(g1[a:e]), m1[a:e], rtol=1e-10, atol=1e-300), name
+
+
+def _grad_with_gates(p, x, preds, succs, labels, L, flip_layers):
+    """The float64 gradient with the uncertain ReLU gates (|z| below 5% of its sum of
+    |terms|) of the given layers set the other way, written out here: the backward pass of
+    the network with those gate values, activations left as they are."""
+    P = G.unpack(p)
+    logits, cache = G.forward(p, x, preds, succs, L, bf=False)
+    lab = np.asarray(labels)
+    mask = (lab >= 0) & (lab < L)
+    n = int(mask.sum())
+    z = logits - logits.max(axis=1, keepdims=True)
+    sm = np.exp(z) / np.exp(z).sum(axis=1, keepdims=True)
+    dz = sm.copy()
+    dz[np.arange(len(lab)), np.where(mask, lab, 0)] -= 1.0
+    dz[~mask] = 0.0
+    dz /= n
+    out = {name: np.zeros(shape) for name, shape in G._SIZES}
+    out["Wh"][:, :L] = cache[2][3].T @ dz
+    out["bh"][:L] = dz.sum(axis=0)
+    dh = dz @ P["Wh"][:, :L].T
+    for l in (2, 1, 0):
+        h_in, A, zl, _ = cache[l]
+        W = P[f"W{l + 1}"]
+        gate = zl > 0
+        if l in flip_layers:
+            unsure = np.abs(zl) <= 0.05 * (np.abs(A) @ np.abs(W) + np.abs(P[f"b{l + 1}"]))
+            gate = gate ^ unsure
+        dZ = dh * gate
+        out[f"W{l + 1}"] = A.T @ dZ
+        out[f"b{l + 1}"] = dZ.sum(axis=0)
+        if l > 0:
+            dh = G.aggregate_T(dZ @ W.T, preds, succs, h_in.shape[1])
+    return G.pack(out)
+
+
+def test_grad_magnitude_flip_bound_covers_a_flipped_gate():
+    """The flip part of grad_magnitude bounds the change of the gradient when ReLU gates
+    near z = 0 go the other way: with a 5% slack, the gradient with every uncertain gate of
+    layers 2 and 3 flipped differs from the oracle's by at most `flip` in every element,
+    and flipping no gate reproduces loss_and_grad."""
+    b, preds, succs, x, p, rng = _tiny(6, n_dags=2)
+    L = 5
+    labels = rng.integers(-1, L, size=b.total_nodes())
+    _, g0 = G.loss_and_grad(p, x, preds, succs, labels, L, bf=False)
+    assert np.allclose(_grad_with_gates(p, x, preds, succs, labels, L, ()), g0, rtol=1e-9,
+                       atol=1e-12 * np.abs(g0).max())
+    _, flip = G.grad_magnitude(p, x, preds, succs, labels, L, bf=False, gate_slack=0.05)
+    g1 = _grad_with_gates(p, x, preds, succs, labels, L, (1, 2))
+    assert np.abs(g1 - g0).max() > 0  # some gates did flip
+    assert (np.abs(g1 - g0) <= flip * (1 + 1e-9) + 1e-12 * np.abs(g0).max()).all()
 
 
 def test_cross_entropy_closed_form_at_zero_head():
