@@ -59,7 +59,11 @@ extern "C" {
 #define DAGRT_VAR_NOPARA 1    /* Alg.1 groups; Eq.5 only, no parallel-node launches */
 #define DAGRT_VAR_NOSEG 2     /* parallel launches of nodes that fit; never segments */
 #define DAGRT_VAR_LITERAL 3   /* Alg.2 with S_j fixed per group and WS_j <- WS_j - C^_c */
-#define DAGRT_N_VARIANTS 4
+#define DAGRT_VAR_NOREPAIR 4  /* as PAPER, but Eq.5's rounded SMs are not trimmed to M: the
+                                 claim after Eq.5 that they fit is taken as it stands; a group
+                                 whose SMs exceed M is bounded by the sum of its members'
+                                 times (the sequential assumption) and launches nothing */
+#define DAGRT_N_VARIANTS 5
 
 /* ---------------------------------------------------------------- limits */
 #define DAGRT_MAX_M 4096
@@ -150,6 +154,19 @@ typedef struct {
                             device like the others); NULL = do not write edges */
     int32_t *extra_src;  /* [extra_off[n_dags]] (v_R, v_n) and (v_n, succ(v_R)) edges */
     int32_t *extra_dst;
+    /* the baselines the Evaluation section compares Theorem 1 with (Sec. 5.2), per DAG,
+     * -1 where status != 0 (the same for every structure variant):
+     *   greedy          Greedy: m_i = min(C^_i, M), nodes assumed sequential: sum_i C_i
+     *   greedy_unaware  Greedy + unaware (the normalisation reference): m_i = C^_i, so
+     *                   Eq.1's wave factor ceil(C^_i / M) applies; sum_i C_i, exact,
+     *                   saturated at 2^63 - 1
+     *   graham_para     Graham_para: every node replaced by C^_i parallel unit loads on one
+     *                   SM each, then Graham's bound L + ceil((sum C^ - L) / M) with L the
+     *                   number of nodes on the longest path (parallel fractions ignored:
+     *                   the units are fully parallel, as in the paper's model) */
+    int64_t *greedy;
+    int64_t *greedy_unaware;
+    int64_t *graham_para;
 } dagrt_schedule_out;
 
 /* Run Alg.1 and Alg.2 with structure variant `variant` on every DAG of the batch, evaluate
@@ -161,6 +178,17 @@ typedef struct {
  * value covers launch errors only. */
 int dagrt_schedule(dagrt_batch *batch, int32_t variant, const dagrt_schedule_out *out,
                    uint32_t flags);
+
+/* Schedulability (System Model, Sec. 2: a periodic task tau = {G, T, D} with an implicit
+ * deadline D = T is schedulable when its makespan bound R(G) <= D). For the bounds of the
+ * batch's last dagrt_schedule(variant): ok[d] = 1 iff DAG d's schedule succeeded and its
+ * bound is at most deadline[d] ticks, else 0; *n_ok = the number of such DAGs.
+ *   deadline [n_dags] int64 (required), ok [n_dags] int32 (may be NULL), n_ok (may be NULL)
+ * flags: DAGRT_PTR_DEVICE if all three are device pointers (then only enqueued); host
+ * pointers are copied and the call synchronises. Returns DAGRT_E_INVAL if the variant was
+ * not scheduled on the batch. */
+int dagrt_schedulable(dagrt_batch *batch, int32_t variant, const int64_t *deadline, int32_t *ok,
+                      int64_t *n_ok, uint32_t flags);
 
 /* Bound of candidate allocations on fixed schedule structures (Lemma 1 / Theorem 1 on a
  * schedule whose SMs per node are given): per group, max C_i if the group's SMs fit in M,

@@ -17,7 +17,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, E_INVAL, E_CYCLE, E_RANGE, E_OOM, E_CAP = 0, -1, -2, -3, -4, -7
-VAR_PAPER, VAR_NOPARA, VAR_NOSEG, VAR_LITERAL = 0, 1, 2, 3
+VAR_PAPER, VAR_NOPARA, VAR_NOSEG, VAR_LITERAL, VAR_NOREPAIR = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -69,6 +69,8 @@ def lib():
         _lib.or_exhaustive_plan.restype = None
         _lib.or_exhaustive_plan.argtypes = [C.c_int32, _P64, _P32, _P32, _P32, _P32, C.c_int32, C.c_int32, _PU8,
                                             C.c_int64, _P64]
+        _lib.or_baselines.restype = C.c_int
+        _lib.or_baselines.argtypes = [C.c_int32, _P32, _P32, _P64, _PU8, C.c_int32, _P64]
         _lib.or_schedule_batch.restype = C.c_int64
         _lib.or_schedule_batch.argtypes = [C.c_int32, _P64, _P64, _P32, _P32, _P64, _PU8, C.c_int32,
                                            C.c_int32, _P64, _P32]
@@ -138,6 +140,19 @@ def schedule(row_ptr, col, wcet, k64, M: int, variant: int = VAR_PAPER, extra_ca
     ne = min(int(o.n_extra), len(es)) if (extra_cap != 0) else 0
     res["extra"] = np.stack([es[:ne], ed[:ne]], axis=1) if ne else np.zeros((0, 2), np.int32)
     return rc, res
+
+
+def baselines(row_ptr, col, wcet, k64, M: int):
+    """(status, greedy, greedy_unaware, graham_para): the Evaluation section's baseline
+    bounds of one DAG (see or_baselines)."""
+    row_ptr = np.ascontiguousarray(row_ptr, np.int32)
+    col = np.ascontiguousarray(col if len(col) else np.zeros(1, np.int32), np.int32)
+    wcet = np.ascontiguousarray(wcet, np.int64)
+    k64 = np.ascontiguousarray(k64, np.uint8)
+    out = np.zeros(3, np.int64)
+    rc = lib().or_baselines(len(wcet), _ptr(row_ptr, _P32), _ptr(col, _P32), _ptr(wcet, _P64), _ptr(k64, _PU8),
+                            int(M), _ptr(out, _P64))
+    return (int(rc), int(out[0]), int(out[1]), int(out[2])) if rc == OK else (int(rc), -1, -1, -1)
 
 
 def bound_plan(plan: dict, M: int, alloc=None, stride: int = 1) -> int:

@@ -21,7 +21,9 @@
  *  - Rule 2: if some head picked by Top_M has m^max = C^ >= M, the group is that
  *    head alone (largest C^, ties: first in Top_M order).
  *  - Eq.5 rounds half up on the exact rational, clamps to >= 1 and, if the group's
- *    SM sum exceeds M, decrements the largest m (ties: higher id) until it fits.
+ *    SM sum exceeds M, decrements the largest m (ties: higher id) until it fits. Variant 4
+ *    leaves the rounded SMs as they are; a group whose SMs then exceed M is bounded by the
+ *    sum of its members' times (the sequential assumption) and launches no parallel node.
  *  - Launching parallel nodes (Alg.2) spends the REMAINING SMs: after each launch
  *    S <- S - m_c. The literal form (S fixed, WS <- WS - C^_c) is variant 3.
  *  - A parallel node is split iff it cannot finish within R(pi_j) on min(C^, S)
@@ -55,6 +57,7 @@
 #define OR_VAR_NOPARA 1  /* Alg.1 groups only, no parallel-node launches */
 #define OR_VAR_NOSEG 2   /* parallel launches that fit, never split */
 #define OR_VAR_LITERAL 3 /* Alg.2 with S_j fixed and WS_j <- WS_j - C^_c */
+#define OR_VAR_NOREPAIR 4 /* Alg.2 with Eq.5's rounded SMs left as they are */
 
 typedef struct {
     /* per node, capacity V */
@@ -177,7 +180,7 @@ int or_schedule_dag(int32_t V, const int32_t *row_ptr, const int32_t *col,
     out->n_join = out->n_groups = out->n_seg = out->n_rows = 0;
     out->n_extra = 0;
     out->bound = 0;
-    if (variant < 0 || variant > 3) return OR_E_INVAL;
+    if (variant < 0 || variant > 4) return OR_E_INVAL;
     int rc = or_validate(V, row_ptr, E, col, wcet, k64, M);
     if (rc != OR_OK) return rc;
     if (V == 0) return OR_OK;
@@ -378,21 +381,25 @@ int or_schedule_dag(int32_t V, const int32_t *row_ptr, const int32_t *col,
             mm[v] = (int32_t)(rem[v] < r ? rem[v] : r);
             sum_m += mm[v];
         }
-        while (sum_m > M) {
+        while (variant != OR_VAR_NOREPAIR && sum_m > M) {
             int32_t best = -1;
             for (int32_t i = 0; i < np; i++)
                 if (best < 0 || mm[P[i]] >= mm[best]) best = P[i]; /* ties: higher id */
             mm[best]--; sum_m--;
         }
         /* Eq.1 per member, Lemma 1: R(pi_j) = max C_i; v_R = lowest id with max C */
-        int64_t R = 0; int32_t vR = -1;
+        int64_t R = 0, sum_c = 0; int32_t vR = -1;
         for (int32_t i = 0; i < np; i++) {
             int32_t v = P[i];
             C[v] = or_exec_time(rem[v], k64[v], mm[v], M);
+            sum_c += C[v];
             if (C[v] > R) { R = C[v]; vR = v; }
         }
+        /* a group whose SMs exceed M (possible only without the repair) runs its members
+         * one after another: R is their summed time */
+        if (sum_m > M) R = sum_c;
         /* Eq.6: remaining SMs and spare capacity */
-        int64_t S = M - sum_m;
+        int64_t S = sum_m < M ? M - sum_m : 0;
         int64_t WS = R * S;
 
         /* Eq.7: released, unfinished nodes outside pi_j, by descending W^anc */
@@ -623,4 +630,69 @@ void or_exhaustive_plan(int32_t n_rows, const int64_t *row_load, const int32_t *
         out[a] = or_bound_plan(n_rows, row_load, row_k, row_m0, row_group, M, alloc, 1);
     }
     free(alloc);
+}
+
+/* ------------------------------------------------------- baselines (Sec. 5.2) */
+
+/* Eq.1 (with the parallel fraction) for any m, in 128-bit arithmetic, saturated at
+ * 2^63 - 1: Greedy + unaware gives a kernel C^ SMs, far above M. */
+static int64_t exec_time_wide(int64_t load, int64_t k, int64_t m, int64_t M)
+{
+    unsigned __int128 waves = (unsigned __int128)((m + M - 1) / M);
+    unsigned __int128 num = waves * (unsigned __int128)load * (unsigned __int128)(64 * m - k * (m - 1));
+    unsigned __int128 den = (unsigned __int128)(64 * m);
+    unsigned __int128 c = (num + den - 1) / den;
+    if (c < 1) c = 1;
+    return c > (unsigned __int128)INT64_MAX ? INT64_MAX : (int64_t)c;
+}
+
+/* The three baselines the Evaluation section compares Theorem 1 with, for one DAG:
+ *   out[0] Greedy: every kernel on m = min(C^, M) SMs, kernels one after another;
+ *   out[1] Greedy + unaware: every kernel on m = C^ SMs (Eq.1's waves apply), one after
+ *          another (saturated at 2^63 - 1);
+ *   out[2] Graham_para: every kernel replaced by C^ unit loads on one SM each, Graham's
+ *          bound L + (vol - L) / M rounded up, with L the number of nodes on the longest
+ *          path and vol the sum of C^.
+ * Returns OR_OK or the validation / cycle error (outputs untouched then). */
+int or_baselines(int32_t V, const int32_t *row_ptr, const int32_t *col, const int64_t *wcet,
+                 const uint8_t *k64, int32_t M, int64_t *out)
+{
+    int64_t E = V > 0 ? row_ptr[V] : 0;
+    int rc = or_validate(V, row_ptr, E, col, wcet, k64, M);
+    if (rc != OR_OK) return rc;
+    /* longest path in nodes, by relaxing edges in a topological order (Kahn) */
+    int32_t *indeg = calloc(V > 0 ? V : 1, sizeof *indeg), *order = calloc(V > 0 ? V : 1, sizeof *order);
+    int64_t *len = calloc(V > 0 ? V : 1, sizeof *len);
+    for (int64_t e = 0; e < E; e++) indeg[col[e]]++;
+    int32_t head = 0, tail = 0;
+    for (int32_t v = 0; v < V; v++) {
+        len[v] = 1;
+        if (indeg[v] == 0) order[tail++] = v;
+    }
+    while (head < tail) {
+        int32_t u = order[head++];
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; e++) {
+            int32_t s = col[e];
+            if (len[u] + 1 > len[s]) len[s] = len[u] + 1;
+            if (--indeg[s] == 0) order[tail++] = s;
+        }
+    }
+    if (tail != V) {
+        free(indeg); free(order); free(len);
+        return OR_E_CYCLE;
+    }
+    int64_t greedy = 0, unaware = 0, vol = 0, L = 0;
+    for (int32_t v = 0; v < V; v++) {
+        int64_t m = wcet[v] < M ? wcet[v] : M;
+        greedy += or_exec_time(wcet[v], k64[v], m, M);
+        int64_t u = exec_time_wide(wcet[v], k64[v], wcet[v], M);
+        unaware = (unaware > INT64_MAX - u) ? INT64_MAX : unaware + u;
+        vol += wcet[v];
+        if (len[v] > L) L = len[v];
+    }
+    out[0] = greedy;
+    out[1] = unaware;
+    out[2] = V > 0 ? L + (vol - L + M - 1) / M : 0;
+    free(indeg); free(order); free(len);
+    return OR_OK;
 }

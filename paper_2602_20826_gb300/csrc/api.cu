@@ -612,6 +612,8 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
         {o.row_load, (void **)&dv.row_load, 16 * nn},  {o.extra_off, (void **)&dv.extra_off, 8 * (nd + 1)},
         {o.extra_src, (void **)&dv.extra_src, 4 * (size_t)n_extra_cap},
         {o.extra_dst, (void **)&dv.extra_dst, 4 * (size_t)n_extra_cap},
+        {o.greedy, (void **)&dv.greedy, 8 * nd},       {o.greedy_unaware, (void **)&dv.greedy_unaware, 8 * nd},
+        {o.graham_para, (void **)&dv.graham_para, 8 * nd},
     };
     if ((o.seg_parent || o.seg_load || o.seg_m || o.seg_group) &&
         !(o.seg_parent && o.seg_load && o.seg_m && o.seg_group))
@@ -699,6 +701,46 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
     for (size_t d = 0; d < nd; d++)
         if (st[d] != DAGRT_OK)
             return fail(ctx, st[d], "dagrt_schedule: DAG %zu failed with status %d", d, st[d]);
+    return DAGRT_OK;
+}
+
+// ------------------------------------------------------------------ schedulability
+extern "C" int dagrt_schedulable(dagrt_batch *b, int32_t variant, const int64_t *deadline, int32_t *ok,
+                                 int64_t *n_ok, uint32_t flags) {
+    NvtxRange nvtx_range_("dagrt_schedulable");
+    if (!b) return DAGRT_E_INVAL;
+    dagrt_ctx *ctx = b->ctx;
+    if (flags & ~DAGRT_PTR_DEVICE) return fail(ctx, DAGRT_E_INVAL, "dagrt_schedulable: unknown flags 0x%x", flags);
+    if (int rc = refuse_in_capture(ctx, !(flags & DAGRT_PTR_DEVICE), "dagrt_schedulable")) return rc;
+    if (variant < 0 || variant >= DAGRT_N_VARIANTS || !b->plan[variant].valid)
+        return fail(ctx, DAGRT_E_INVAL, "dagrt_schedulable: variant %d was not scheduled on this batch", variant);
+    if (!deadline && b->n_dags > 0) return fail(ctx, DAGRT_E_INVAL, "dagrt_schedulable: deadline is NULL");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const Plan &p = b->plan[variant];
+    const bool dev = (flags & DAGRT_PTR_DEVICE) != 0;
+    const size_t nd = b->n_dags;
+    const int64_t *d_dl = deadline;
+    int32_t *d_ok = ok;
+    unsigned long long *d_n = (unsigned long long *)n_ok;
+    if (!dev) {  // stage: [deadline | ok | count]
+        const size_t a8 = (8 * nd + 255) / 256 * 256, a4 = (4 * nd + 255) / 256 * 256;
+        int rc = ensure_tmp(b, a8 + a4 + 256);
+        if (rc) return rc;
+        char *t = (char *)b->tmp;
+        d_dl = (const int64_t *)t;
+        d_ok = ok ? (int32_t *)(t + a8) : nullptr;
+        d_n = (unsigned long long *)(t + a8 + a4);
+        if (nd) CK(cudaMemcpyAsync((void *)d_dl, deadline, 8 * nd, cudaMemcpyHostToDevice, ctx->stream), "copy deadlines");
+    }
+    if (d_n) CK(cudaMemsetAsync(d_n, 0, 8, ctx->stream), "clear count");
+    CK(sched_schedulable(b->n_dags, p.status, p.bound, d_dl, d_ok, d_n, ctx->n_sm, ctx->stream), "schedulability");
+    ctx->launches += nd > 0;
+    if (dev) return DAGRT_OK;
+    if (ok && nd) CK(cudaMemcpyAsync(ok, d_ok, 4 * nd, cudaMemcpyDeviceToHost, ctx->stream), "copy flags");
+    int64_t cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, d_n, 8, cudaMemcpyDeviceToHost, ctx->stream), "copy count");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    if (n_ok) *n_ok = cnt;
     return DAGRT_OK;
 }
 

@@ -161,6 +161,24 @@ __device__ inline void write_failure(const SchedArgs &a, int d, int code) {
     if (a.o.n_seg) a.o.n_seg[d] = 0;
     if (a.o.n_rows) a.o.n_rows[d] = 0;
     if (a.o.n_extra) a.o.n_extra[d] = 0;
+    if (a.o.greedy) a.o.greedy[d] = -1;
+    if (a.o.greedy_unaware) a.o.greedy_unaware[d] = -1;
+    if (a.o.graham_para) a.o.graham_para[d] = -1;
+}
+
+// Greedy + unaware kernel time (baseline of the Evaluation section): the kernel runs on
+// m = x SMs whatever M is, so Eq.1's wave factor ceil(x / M) applies. Exact in 128-bit
+// arithmetic, saturated at 2^63 - 1.
+__device__ __forceinline__ uint64_t exec_time_unaware(uint64_t x, uint32_t k, uint32_t M) {
+    const unsigned __int128 waves = (x + M - 1) / M;
+    const unsigned __int128 num = waves * x * (64ull * x - (uint64_t)k * (x - 1));
+    const unsigned __int128 den = 64ull * x;
+    const unsigned __int128 c = (num + den - 1) / den;
+    return c > (unsigned __int128)INT64_MAX ? (uint64_t)INT64_MAX : (c < 1 ? 1ull : (uint64_t)c);
+}
+__device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b) {
+    const uint64_t s = a + b;
+    return s > (uint64_t)INT64_MAX || s < a ? (uint64_t)INT64_MAX : s;
 }
 
 // plan row r: `id` is the node (< V) or segment (>= V) it runs, `owner` the node whose
@@ -365,7 +383,9 @@ __device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int
                     ws.mm[v] = (uint16_t)m;
                     sum_m += m;
                 }
-                while (sum_m > M) {  // keep sum m_i <= M: trim the largest m (ties: higher id)
+                // keep sum m_i <= M: trim the largest m (ties: higher id); the no-repair
+                // variant leaves the rounded SMs as they are
+                while (g.variant != DAGRT_VAR_NOREPAIR && sum_m > M) {
                     int best = -1;
                     for (int i = gb; i < ge; i++) {
                         const int v = ws.gmem[i];
@@ -376,12 +396,14 @@ __device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int
                     sum_m--;
                 }
                 // Eq.1 per member and Lemma 1: R(pi_j) = max C_i, v_R = lowest id with C_i = R
+                uint64_t csum = 0;
                 for (int i = gb; i < ge; i++) {
                     const int v = ws.gmem[i];
                     if (ws.st[v] & ST_DONE) continue;
                     const uint32_t x = ws.rem[v], m = ws.mm[v];
                     const uint64_t c =
                         (x == ws.load[v] && m == (x < M ? x : M)) ? ws.cfull[v] : exec_time(x, ws.kk[v], m, M);
+                    csum += c;
                     if (c > R) {
                         R = c;
                         vR = v;
@@ -389,16 +411,18 @@ __device__ void group_serial(const Ws &ws, const SchedArgs &a, const Dag &g, int
                     acc.lastr = acc.nrows;
                     acc.lastz = write_row(a, g, acc.nrows++, v, v, j, x, ws.kk[v], m, c);
                 }
+                if (sum_m > M) R = csum;  // over-full (no repair): members one after another
             }
         }
         if (np == 0) {  // every member already ran as a parallel node: the group is dropped
             if (a.o.group_R) a.o.group_R[g.n0 + j] = 0;
         } else {
             int nl, nwhole;
+            const uint32_t S0 = sum_m < M ? M - sum_m : 0u;
             if (g.W > kSumWords)
-                launch_parallel<true>(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
+                launch_parallel<true>(ws, a, g, j, R, S0, acc, &nl, &nwhole);
             else
-                launch_parallel<false>(ws, a, g, j, R, M - sum_m, acc, &nl, &nwhole);
+                launch_parallel<false>(ws, a, g, j, R, S0, acc, &nl, &nwhole);
             extra_edges(ws, a, g, j, vR, np, nl, nwhole, acc);
             nf = ge - gb + nl;  // candidates to finish: the members, then the launched parts
             if (a.o.group_R) a.o.group_R[g.n0 + j] = (int64_t)R;
@@ -491,7 +515,7 @@ __device__ void group_team(const Team<NT> &tm, const Ws &ws, const SchedArgs &a,
     }
     uint64_t sum_m = tm.sum(sml);
     tm.sync();
-    while (sum_m > M) {
+    while (g.variant != DAGRT_VAR_NOREPAIR && sum_m > M) {
         uint64_t key = 0;
         for (int i = gb + tm.t; i < ge; i += NT) {
             const int v = ws.gmem[i];
@@ -504,16 +528,19 @@ __device__ void group_team(const Team<NT> &tm, const Ws &ws, const SchedArgs &a,
         sum_m--;
         tm.sync();
     }
-    uint64_t ckey = 0;  // (C, 0xffff - id): the max is the largest C, then the lowest id
+    uint64_t ckey = 0, csum = 0;  // (C, 0xffff - id): the max is the largest C, then the lowest id
     for (int i = gb + tm.t; i < ge; i += NT) {
         const int v = ws.gmem[i];
         if (ws.st[v] & ST_DONE) continue;
         const uint64_t c = exec_time(ws.rem[v], ws.kk[v], ws.mm[v], M);
         const uint64_t kv = (c << 16) | (uint64_t)(0xffff - v);
         ckey = kv > ckey ? kv : ckey;
+        csum += c;
     }
     ckey = tm.maxu(ckey);
-    const uint64_t R = ckey >> 16;
+    csum = tm.sum(csum);
+    // over-full (no repair only): the members run one after another
+    const uint64_t R = sum_m > M ? csum : ckey >> 16;
     const int vR = 0xffff - (int)(ckey & 0xffff);
     int nrows = sc[8];
     for (int base = gb; base < ge; base += NT) {
@@ -533,10 +560,11 @@ __device__ void group_team(const Team<NT> &tm, const Ws &ws, const SchedArgs &a,
         acc.nrows = nrows;
         acc.lastr = -1;  // the members' rows were written by the team
         int nl, nwhole;
+        const uint32_t S0 = sum_m < M ? M - (uint32_t)sum_m : 0u;
         if (g.W > kSumWords)
-            launch_parallel<true>(ws, a, g, j, R, M - (uint32_t)sum_m, acc, &nl, &nwhole);
+            launch_parallel<true>(ws, a, g, j, R, S0, acc, &nl, &nwhole);
         else
-            launch_parallel<false>(ws, a, g, j, R, M - (uint32_t)sum_m, acc, &nl, &nwhole);
+            launch_parallel<false>(ws, a, g, j, R, S0, acc, &nl, &nwhole);
         extra_edges(ws, a, g, j, vR, (int)np, nl, nwhole, acc);
         sc[1] = nl;
         sc[6] = 0;
@@ -662,6 +690,9 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             if (a.o.n_seg) a.o.n_seg[d] = 0;
             if (a.o.n_rows) a.o.n_rows[d] = 0;
             if (a.o.n_extra) a.o.n_extra[d] = 0;
+            if (a.o.greedy) a.o.greedy[d] = 0;
+            if (a.o.greedy_unaware) a.o.greedy_unaware[d] = 0;
+            if (a.o.graham_para) a.o.graham_para[d] = 0;
         }
         return;
     }
@@ -1010,16 +1041,28 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
 
     // ---- Alg.2 over the groups in order, with Lemma 1 and Theorem 1
     int nsrc = 0;
+    const bool want_base = a.o.greedy || a.o.greedy_unaware || a.o.graham_para;
+    uint64_t b_greedy = 0, b_unaware = 0, b_vol = 0;  // baseline sums (Evaluation section)
     for (int v = tm.t; v < V; v += NT) {
         const uint32_t x = ws.load[v];
         ws.rem[v] = x;
         ws.cfull[v] = (uint32_t)exec_time(x, ws.kk[v], x < M ? x : M, M);
+        if (want_base) {
+            b_greedy += ws.cfull[v];
+            b_unaware = sat_add(b_unaware, exec_time_unaware(x, ws.kk[v], M));
+            b_vol += x;
+        }
         ws.cnt[v] = ws.indeg[v];  // predecessors not yet finished
         ws.st[v] = 0;
         ws.mm[v] = 0;
         nsrc += ws.indeg[v] == 0;
     }
     nsrc = (int)tm.sum(nsrc);
+    if (want_base) {
+        b_greedy = tm.sum(b_greedy);
+        b_unaware = tm.reduce(b_unaware, [](uint64_t p, uint64_t q) { return sat_add(p, q); });
+        b_vol = tm.sum(b_vol);
+    }
     for (int w = tm.t; w < W; w += NT) ws.relmask[w] = 0;
     for (int w = tm.t; w < (W + 63) / 64; w += NT) ws.relsum[w] = 0;
     tm.sync();
@@ -1089,6 +1132,12 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         if (a.o.n_seg) a.o.n_seg[d] = acc.nseg;
         if (a.o.n_rows) a.o.n_rows[d] = acc.nrows;
         if (a.o.n_extra) a.o.n_extra[d] = acc.nextra;
+        // baselines: Greedy (sequential, m = min(C^, M)), Greedy + unaware (sequential,
+        // m = C^), Graham_para (unit-load nodes: L + ceil((vol - L) / M), L = nodes on the
+        // longest path)
+        if (a.o.greedy) a.o.greedy[d] = (int64_t)b_greedy;
+        if (a.o.greedy_unaware) a.o.greedy_unaware[d] = (int64_t)b_unaware;
+        if (a.o.graham_para) a.o.graham_para[d] = (int64_t)(nlev + (b_vol - nlev + M - 1) / M);
     }
     for (int v = tm.t; v < V; v += NT) {
         if (a.o.block_of) a.o.block_of[n0 + v] = ws.blk[v];
@@ -1202,6 +1251,33 @@ cudaError_t sched_launch_cta_smem(const SchedArgs &a, int n_sm, cudaStream_t st)
     int grid = n_sm * per_sm;
     if (grid > a.n_list) grid = a.n_list;
     k_sched_cta<kCtaThreads, true><<<grid, kCtaThreads, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ schedulability
+__global__ void k_schedulable(int32_t n_dags, const int32_t *status, const int64_t *bound, const int64_t *deadline,
+                              int32_t *ok, unsigned long long *n_ok) {
+    __shared__ unsigned int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    unsigned int mine = 0;
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n_dags; d += gridDim.x * blockDim.x) {
+        const bool y = status[d] == DAGRT_OK && bound[d] <= deadline[d];
+        if (ok) ok[d] = y ? 1 : 0;
+        mine += y;
+    }
+    mine = __reduce_add_sync(FULL, mine);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_cnt, mine);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt && n_ok) atomicAdd(n_ok, (unsigned long long)s_cnt);
+}
+
+cudaError_t sched_schedulable(int32_t n_dags, const int32_t *status, const int64_t *bound, const int64_t *deadline,
+                              int32_t *ok, unsigned long long *n_ok, int n_sm, cudaStream_t st) {
+    if (n_dags < 1) return cudaSuccess;
+    int grid = (n_dags + 255) / 256;
+    if (grid > 4 * n_sm) grid = 4 * n_sm;
+    k_schedulable<<<grid, 256, 0, st>>>(n_dags, status, bound, deadline, ok, n_ok);
     return cudaGetLastError();
 }
 

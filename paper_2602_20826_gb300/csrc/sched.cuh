@@ -57,4 +57,9 @@ cudaError_t sched_launch_cta(const SchedArgs &a, int grid, cudaStream_t st);
 int64_t sched_smem_limit();
 cudaError_t sched_launch_cta_smem(const SchedArgs &a, int n_sm, cudaStream_t st);
 
+// Schedulability of implicit-deadline tasks: ok[d] = status[d] == OK && bound[d] <=
+// deadline[d]; *n_ok (zeroed by the caller) += the number of such DAGs.
+cudaError_t sched_schedulable(int32_t n_dags, const int32_t *status, const int64_t *bound, const int64_t *deadline,
+                              int32_t *ok, unsigned long long *n_ok, int n_sm, cudaStream_t st);
+
 }  // namespace dagrt

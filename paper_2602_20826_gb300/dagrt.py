@@ -25,7 +25,7 @@ lib = C.CDLL(_LIB_PATH)
 
 OK, E_INVAL, E_CYCLE, E_RANGE, E_OOM, E_DEVICE, E_TIMEOUT, E_CAP, E_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7, -8
 PTR_DEVICE = 1
-VAR_PAPER, VAR_NOPARA, VAR_NOSEG, VAR_LITERAL = 0, 1, 2, 3
+VAR_PAPER, VAR_NOPARA, VAR_NOSEG, VAR_LITERAL, VAR_NOREPAIR = 0, 1, 2, 3, 4
 MAX_M, MAX_V = 4096, 65535
 
 _vp = C.c_void_p
@@ -35,7 +35,8 @@ class dagrt_schedule_out(C.Structure):
     _fields_ = [(n, _vp) for n in (
         "bound", "status", "n_groups", "n_seg", "n_rows", "n_extra", "level", "wanc", "block_of",
         "group_of", "exec_group", "m", "group_R", "seg_parent", "seg_load", "seg_m", "seg_group",
-        "row_id", "row_group", "row_m0", "row_load", "extra_off", "extra_src", "extra_dst")]
+        "row_id", "row_group", "row_m0", "row_load", "extra_off", "extra_src", "extra_dst",
+        "greedy", "greedy_unaware", "graham_para")]
 
 
 def _sig(name, res, args):
@@ -57,6 +58,7 @@ dagrt_batch_free = _sig("dagrt_batch_free", None, [_vp])
 dagrt_batch_n_dags = _sig("dagrt_batch_n_dags", C.c_int32, [_vp])
 dagrt_batch_total_nodes = _sig("dagrt_batch_total_nodes", C.c_int64, [_vp])
 dagrt_schedule = _sig("dagrt_schedule", C.c_int, [_vp, C.c_int32, C.POINTER(dagrt_schedule_out), C.c_uint32])
+dagrt_schedulable = _sig("dagrt_schedulable", C.c_int, [_vp, C.c_int32, _vp, _vp, C.POINTER(C.c_int64), C.c_uint32])
 dagrt_bound = _sig("dagrt_bound", C.c_int,
                    [_vp, C.c_int32, C.POINTER(C.c_int32), C.c_int32, _vp, C.c_int64, _vp, _vp, _vp, C.c_uint32])
 SEARCH_RANDOM, SEARCH_EXHAUSTIVE, SEARCH_PERTURB = 0, 1, 2
@@ -130,7 +132,8 @@ def _is_device(x):
 
 # per-node / per-DAG output fields and their dtypes
 _DAG_FIELDS = {"bound": np.int64, "status": np.int32, "n_groups": np.int32, "n_seg": np.int32,
-               "n_rows": np.int32, "n_extra": np.int64}
+               "n_rows": np.int32, "n_extra": np.int64, "greedy": np.int64, "greedy_unaware": np.int64,
+               "graham_para": np.int64}
 _NODE_FIELDS = {"level": np.int32, "wanc": np.int64, "block_of": np.int32, "group_of": np.int32,
                 "exec_group": np.int32, "m": np.int32, "group_R": np.int64, "seg_parent": np.int32,
                 "seg_load": np.int64, "seg_m": np.int32, "seg_group": np.int32}
@@ -310,6 +313,15 @@ class LoadedBatch:
             if f in _DAG_FIELDS:
                 res[f] = res[f][:nd]
         return res
+
+    def schedulable(self, variant: int, deadline):
+        """dagrt_schedulable with host arrays: (ok flags int32 [n_dags], number schedulable)."""
+        dl = np.ascontiguousarray(deadline, np.int64)
+        assert dl.shape == (self.n_dags,)
+        ok = np.zeros(max(self.n_dags, 1), np.int32)
+        n = C.c_int64(0)
+        self.ctx.check(dagrt_schedulable(self.h, int(variant), _ptr(dl), _ptr(ok), C.byref(n), 0))
+        return ok[:self.n_dags], int(n.value)
 
     def bound(self, variant_ids, n_alloc: int, m_alloc, cand_stride: int, out_bound=None,
               best_bound=None, best_cand=None, want_all: bool = True):

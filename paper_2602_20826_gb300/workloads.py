@@ -200,6 +200,31 @@ def paper_layered_edges(rng, depth: int, P: int):
     return V, np.asarray(src, np.int64), np.asarray(dst, np.int64)
 
 
+def paper_layered_batch(n_dags: int, P: int, M: int, c_avg: int, seed: int, depth_lo: int = 5,
+                        depth_hi: int = 8, name: str = "paper-layered") -> Batch:
+    """The paper's synthetic set-up: per DAG a depth uniform in [depth_lo, depth_hi] and
+    layers of width U[2, P] between a single source and a single sink (paper_layered_edges),
+    node loads uniform on [1, 2 c_avg - 1] (mean c_avg), fully parallel kernels (k = 64)."""
+    dags = []
+    for d in range(n_dags):
+        rng = _rng(seed, d)
+        depth = int(rng.integers(depth_lo, depth_hi + 1))
+        V, s, t = paper_layered_edges(rng, depth, P)
+        rp, col = csr_from_edges(V, s, t)
+        w = rng.integers(1, 2 * c_avg, size=V).astype(np.int64)
+        dags.append((rp, col, w, np.full(V, 64, np.uint8)))
+    return from_dags(dags, M, name)
+
+
+def implicit_deadlines(batch: Batch, utilisation: float) -> np.ndarray:
+    """Implicit deadlines D = T of a periodic task per DAG at normalised utilisation U:
+    T = ceil(sum of C^ / (M U)) ticks (the DAG's work over the GPU's capacity in one
+    period)."""
+    vol = np.add.reduceat(batch.wcet, batch.node_off[:-1]) if batch.total_nodes() else np.zeros(batch.n_dags)
+    vol = np.where(np.diff(batch.node_off) > 0, vol, 0).astype(np.float64)
+    return np.ceil(vol / (batch.M * float(utilisation))).astype(np.int64)
+
+
 # ---------------------------------------------------------------- batch configs
 
 def _rng(seed: int, d: int):

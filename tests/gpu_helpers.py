@@ -8,7 +8,7 @@ import oracle
 
 FIELDS = ("bound", "status", "n_groups", "n_seg", "n_rows", "n_extra", "level", "wanc", "block_of",
           "group_of", "exec_group", "m", "group_R", "seg_parent", "seg_load", "seg_m", "seg_group",
-          "row_id", "row_group", "row_m0", "row_load")
+          "row_id", "row_group", "row_m0", "row_load", "greedy", "greedy_unaware", "graham_para")
 
 
 def context():
@@ -34,6 +34,10 @@ def compare_dag(batch, res, d, variant=0, edges=True):
     n0 = int(batch.node_off[d])
     V = batch.n_nodes(d)
     assert res["status"][d] == rc, (d, res["status"][d], rc)
+    if "greedy" in res:  # the Evaluation section's baselines (-1 for a failed DAG)
+        rb, g, u, gr = oracle.baselines(*batch.dag(d), batch.M)
+        want = (g, u, gr) if rb == 0 else (-1, -1, -1)
+        assert (res["greedy"][d], res["greedy_unaware"][d], res["graham_para"][d]) == want, (d, want)
     if rc != 0:
         assert res["bound"][d] == -1
         return ref

@@ -7,7 +7,7 @@ accumulates in float64. The two differ by fp32 accumulation error (~1e-6 relativ
 rarely, by one bfloat16 step (2^-8 relative) where a value lies within that error of a
 rounding boundary. The bounds below allow a few such steps per logit; the backward pass
 also rounds dZ to bfloat16 for its MMAs (2^-9 relative per element), so every gradient
-element is held to 2^-7 of the sum of the absolute values of the products it adds up
+element is held to 2^-6 of the sum of the absolute values of the products it adds up
 (oracle.gnn.grad_magnitude: the backward pass on absolute values), plus the whole term of
 every ReLU gate that fp32 rounding could set the other way, on top of a 2% bound on each
 parameter block's norm."""
@@ -111,15 +111,16 @@ def test_gradient_matches_oracle(setup):
     p = model.params().astype(np.float64)
     rl, rg = G.loss_and_grad(p, x, preds, succs, labels, L, bf=True)
     assert abs(loss - rl) <= 1e-3 * max(1.0, rl), (loss, rl)
-    # element by element: |g - g_ref| <= 2^-7 * (sum of |products| behind the element),
-    # i.e. a few bf16 roundings (2^-9 relative each: dZ for the MMAs, the stored
-    # activations) of every term the element sums, carried through the layers; ReLU gates
-    # whose z lies within 2^-7 of its sum of |terms| count as open (fp32 sums and one-step
-    # bf16 flips of a layer's input move z by less than that, so such a gate may differ)
-    mag, flip = G.grad_magnitude(p, x, preds, succs, labels, L, bf=True, gate_slack=2.0 ** -7)
+    # element by element: |g - g_ref| <= 2^-6 * (sum of |products| behind the element):
+    # each product's operands differ by at most four bf16 steps of 2^-8 relative between the
+    # two sides (dZ rounded for the MMAs, and one-step flips of the stored activations of
+    # each layer a value passes through), carried through the layers; ReLU gates whose z
+    # lies within 2^-6 of its sum of |terms| count as possibly flipped, with their whole
+    # term allowed (grad_magnitude's flip part)
+    mag, flip = G.grad_magnitude(p, x, preds, succs, labels, L, bf=True, gate_slack=2.0 ** -6)
     assert (np.abs(rg) <= mag * (1 + 1e-9) + 1e-15).all()  # |g| <= sum of |terms|
     err = np.abs(g.astype(np.float64) - rg)
-    tol = 2.0 ** -7 * mag + flip + 1e-9
+    tol = 2.0 ** -6 * mag + flip + 1e-9
     gb, rb, eb, tb = _blocks(g.astype(np.float64)), _blocks(rg), _blocks(err), _blocks(tol)
     for name in rb:
         bad = np.nonzero(eb[name] > tb[name])[0]

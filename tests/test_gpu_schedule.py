@@ -38,7 +38,7 @@ def test_worked_example(ctx):
     assert res["bound"][0] == 5
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("cfg,vlo,vhi,n", [(1, 20, 20, 40), (2, 5, 200, 120), (3, 50, 300, 40),
                                            (4, 100, 400, 12)])
 def test_small_configs_all_outputs(ctx, cfg, vlo, vhi, n, variant):
@@ -46,7 +46,7 @@ def test_small_configs_all_outputs(ctx, cfg, vlo, vhi, n, variant):
     _check_batch(ctx, b, variant)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_random_small_dags_many_M(ctx, variant):
     rng = np.random.default_rng(500 + variant)
     for M in (1, 2, 3, 5, 8, 16, 148, 4096):
@@ -88,7 +88,7 @@ def test_special_shapes(ctx):
     dags.append((rp, col, np.full(60, 2**32 - 1), np.zeros(60, np.uint8)))
     dags.append((rp, col, rng.integers(2**31, 2**32, size=60), np.full(60, 64, np.uint8)))
     for M in (1, 7, 148, 4096):
-        for var in range(4):
+        for var in range(5):
             _check_batch(ctx, wl.from_dags(dags, M), var)
 
 
