@@ -231,10 +231,19 @@ def _rng(seed: int, d: int):
     return np.random.default_rng([int(seed), int(d)])
 
 
+def er_sizes(n_dags: int, v_lo: int, v_hi: int, seed: int) -> np.ndarray:
+    """Node count of every DAG of er_batch(n_dags, v_lo, v_hi, ..., seed): the first draw
+    of each DAG's own stream, without generating the DAG."""
+    return np.asarray([int(_rng(seed, d).integers(v_lo, v_hi + 1)) for d in range(n_dags)], np.int64)
+
+
 def er_batch(n_dags: int, v_lo: int, v_hi: int, p: float, M: int, seed: int,
-             wcet="loguniform", frac_lo: float = 0.3, name: str = "") -> Batch:
+             wcet="loguniform", frac_lo: float = 0.3, name: str = "", ids=None) -> Batch:
+    """Erdos-Renyi DAGs, each from its own stream (seed, d); with `ids` only those DAGs of
+    the n_dags-DAG batch, in the order given (DAG ids[i] is identical to DAG ids[i] of the
+    whole batch)."""
     dags = []
-    for d in range(n_dags):
+    for d in (range(n_dags) if ids is None else ids):
         rng = _rng(seed, d)
         V = int(rng.integers(v_lo, v_hi + 1))
         s, t = er_edges(rng, V, p)
@@ -250,10 +259,14 @@ def er_batch(n_dags: int, v_lo: int, v_hi: int, p: float, M: int, seed: int,
     return from_dags(dags, M, name)
 
 
-def config(idx: int, n_dags: int | None = None, seed: int | None = None) -> Batch:
+def config(idx: int, n_dags: int | None = None, seed: int | None = None, ids=None) -> Batch:
     """The five measured workloads (1-based index). `n_dags` shrinks a batch (same
-    per-DAG streams, so DAG d is identical at every batch size)."""
+    per-DAG streams, so DAG d is identical at every batch size); `ids` (configs 2-4) keeps
+    only those DAGs of the batch."""
     seed = BASE_SEED + idx if seed is None else seed
+    if ids is not None and idx in (2, 3, 4):
+        lo, hi, p = {2: (20, 200, 0.1), 3: (50, 500, 0.05), 4: (100, 1000, 0.05)}[idx]
+        return er_batch(len(ids), lo, hi, p, 148, seed, name=f"cfg{idx}-shard", ids=[int(d) for d in ids])
     if idx == 1:   # single DAG, 20 nodes, p=0.2, WCET U[1,100], f U[0.5,1], M=8
         return er_batch(1 if n_dags is None else n_dags, 20, 20, 0.2, 8, seed,
                         wcet="uniform100", frac_lo=0.5, name="cfg1-er20")
