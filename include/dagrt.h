@@ -282,6 +282,36 @@ int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_
                            const uint8_t *k64, int64_t total_nodes, int64_t total_edges, int32_t M,
                            int32_t variant, int64_t *bound, int32_t *status, void *cuda_stream);
 
+/* ---------------------------------------------------------------- realisation on the GPU
+ * A schedule of one DAG run on this GPU as a CUDA graph, as in the case study of the
+ * Evaluation section (CUDA Graph API; m_i realised through the kernel's launch shape; loads
+ * emulated by one kernel function run for different lengths). Every part of the schedule (a
+ * node's last part, or a parallel segment) is one kernel node whose grid has m CTAs, each
+ * reserving more than half of an SM's shared memory so that the kernel holds m SMs; every
+ * CTA runs for C^ ((1 - f) + f / m) ticks of tick_us microseconds (Eq.1 with Amdahl's
+ * parallel fraction f = k/64, not rounded). Edges: each DAG edge u -> v makes every part of
+ * v wait for u's last part, and a node's segment runs before its residual part; then by
+ * mode
+ *   DAGRT_REALISE_BARRIER  plus a barrier after each group of Pi (the group-by-group
+ *                          execution Theorem 1's proof assumes);
+ *   DAGRT_REALISE_EDGES    plus the extra dependencies of Alg.2 only (the paper's claim
+ *                          that they order the groups);
+ *   DAGRT_REALISE_GREEDY   the Greedy baseline of the case study instead: every kernel on
+ *                          min(C^, M) SMs, only the DAG's edges.
+ * Inputs are one DAG in dagrt_load_csr's layout (host pointers, V >= 1), M <= the device's
+ * SM count, the structure variant (ignored by GREEDY), reps >= 1 timed replays after one
+ * warm-up; makespan_us[reps] receives each replay's time (CUDA events around the graph
+ * launch) and *bound (may be NULL) the bound in ticks: Theorem 1's R(G), or the Greedy
+ * baseline for GREEDY. Synchronous; allocates its own graph and stream. Returns
+ * DAGRT_E_INVAL (bad argument, M above the SM count, a part above M SMs), the schedule's
+ * per-DAG error, DAGRT_E_DEVICE or DAGRT_E_TIMEOUT (a kernel's wait hit its limit). */
+#define DAGRT_REALISE_BARRIER 0
+#define DAGRT_REALISE_EDGES 1
+#define DAGRT_REALISE_GREEDY 2
+int dagrt_realise(dagrt_ctx *ctx, int32_t V, const int32_t *row_ptr, const int32_t *col,
+                  const int64_t *wcet, const uint8_t *k64, int32_t M, int32_t variant, int32_t mode,
+                  float tick_us, int32_t reps, float *makespan_us, int64_t *bound);
+
 /* ---------------------------------------------------------------- batching controls
  * Launch-shape choices of the batched kernels. None of them changes a result: every
  * setting gives bit-identical outputs; they only move work between kernels.

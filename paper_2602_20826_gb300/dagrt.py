@@ -75,6 +75,9 @@ dagrt_schedule_noalloc = _sig("dagrt_schedule_noalloc", C.c_int,
                               [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int64, C.c_int32,
                                C.c_int32, _vp, _vp, _vp])
 
+REALISE_BARRIER, REALISE_EDGES, REALISE_GREEDY = 0, 1, 2
+dagrt_realise = _sig("dagrt_realise", C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32,
+                                                C.c_float, C.c_int32, _vp, C.POINTER(C.c_int64)])
 dagrt_model_n_params = _sig("dagrt_model_n_params", C.c_int64, [])
 dagrt_model_create = _sig("dagrt_model_create", C.c_int, [_vp, C.c_int32, _vp, C.c_uint64, C.POINTER(_vp)])
 dagrt_model_free = _sig("dagrt_model_free", None, [_vp])
@@ -177,6 +180,19 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def realise(self, row_ptr, col, wcet, k64, M: int, mode: int = REALISE_BARRIER, variant: int = VAR_PAPER,
+                tick_us: float = 20.0, reps: int = 10):
+        """dagrt_realise on one DAG (host arrays): (makespans in us [reps], bound in ticks)."""
+        rp = np.ascontiguousarray(row_ptr, np.int32)
+        cl = np.ascontiguousarray(col, np.int32)
+        w = np.ascontiguousarray(wcet, np.int64)
+        k = np.ascontiguousarray(k64, np.uint8)
+        out = np.zeros(reps, np.float32)
+        bnd = C.c_int64(0)
+        self.check(dagrt_realise(self.h, len(w), _ptr(rp), _ptr(cl) if len(cl) else None, _ptr(w), _ptr(k), int(M),
+                                 int(variant), int(mode), C.c_float(tick_us), int(reps), _ptr(out), C.byref(bnd)))
+        return out, int(bnd.value)
 
     def graph_begin(self):
         self.check(dagrt_graph_begin(self.h))

@@ -70,11 +70,50 @@ def run(n_dags: int = 1000, seed: int = 20260226):
     return rows
 
 
+def case_study(reps: int = 100, tick_us: float = 10.0, seed: int = 20260226):
+    """The case study's comparison on this GPU: per setting (M in {8, 30} SMs, mean load 4
+    or 20 ticks), three of the paper's layered DAGs (P = 8) are realised as CUDA graphs
+    (dagrt_realise) `reps` times each, with the proposed schedule under group barriers and
+    with Greedy; max / average / standard deviation of the measured makespans in ms, and
+    Theorem 1's bound (ticks x tick_us) beside them."""
+    import torch
+    from .dagrt import REALISE_BARRIER, REALISE_GREEDY
+    ctx = Context(0, torch.cuda.current_stream().cuda_stream)
+    rows = []
+    for c_avg in (4, 20):
+        for M in (8, 30):
+            b = wl.paper_layered_batch(3, 8, M, c_avg, seed + 17 * M + c_avg)
+            for d in range(b.n_dags):
+                rp, col, w, k = b.dag(d)
+                r = {"sweep": "case_study", "M": M, "c_avg": c_avg, "dag": d, "nodes": len(w), "tick_us": tick_us}
+                for name, mode in (("proposed", REALISE_BARRIER), ("greedy", REALISE_GREEDY)):
+                    ms, bnd = ctx.realise(rp, col, w, k, M, mode, tick_us=tick_us, reps=reps)
+                    ms = ms / 1e3
+                    r[name] = {"max_ms": float(ms.max()), "avg_ms": float(ms.mean()), "std_ms": float(ms.std()),
+                               "bound_ms": bnd * tick_us / 1e3}
+                rows.append(r)
+    ctx.close()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dags", type=int, default=1000)
     ap.add_argument("--json", default=None)
+    ap.add_argument("--case-study", action="store_true", help="realise schedules as CUDA graphs instead")
     args = ap.parse_args()
+    if args.case_study:
+        rows = case_study()
+        for r in rows:
+            p, g = r["proposed"], r["greedy"]
+            print(f"M={r['M']:>2} C_avg={r['c_avg']:>2} dag {r['dag']} ({r['nodes']} nodes)  proposed "
+                  f"{p['max_ms']:.3f}/{p['avg_ms']:.3f}/{p['std_ms']:.4f} ms (bound {p['bound_ms']:.3f})  greedy "
+                  f"{g['max_ms']:.3f}/{g['avg_ms']:.3f}/{g['std_ms']:.4f} ms (bound {g['bound_ms']:.3f})")
+        if args.json:
+            with open(args.json, "w") as f:
+                for r in rows:
+                    f.write(json.dumps(r) + "\n")
+        return
     rows = run(args.dags)
     for r in rows:
         if r["sweep"] == "schedulability":
