@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <set>
 #include <vector>
 
 #include "dagrt.h"
@@ -178,8 +179,9 @@ extern "C" int dagrt_realise(dagrt_ctx *ctx, int32_t V, const int32_t *row_ptr, 
         if (cudaGraphAddKernelNode(&node[i], gg.g, nullptr, 0, &kp) != cudaSuccess) return DAGRT_E_DEVICE;
     }
     std::vector<cudaGraphNode_t> from, to;
+    std::set<std::pair<int, int>> seen;  // a graph may hold each dependency only once
     auto dep = [&](int a, int b) {
-        if (a >= 0 && b >= 0 && a != b) {
+        if (a >= 0 && b >= 0 && a != b && seen.emplace(a, b).second) {
             from.push_back(node[a]);
             to.push_back(node[b]);
         }
