@@ -285,9 +285,11 @@ int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_
 /* ---------------------------------------------------------------- realisation on the GPU
  * A schedule of one DAG run on this GPU as a CUDA graph, as in the case study of the
  * Evaluation section (CUDA Graph API; m_i realised through the kernel's launch shape; loads
- * emulated by one kernel function run for different lengths). Every part of the schedule (a
- * node's last part, or a parallel segment) is one kernel node whose grid has m CTAs, each
- * reserving more than half of an SM's shared memory so that the kernel holds m SMs; every
+ * emulated by one kernel function run for different lengths). The GPU is narrowed to the
+ * model's M SMs: before each replay, filler CTAs (one per SM, each running for a fixed time
+ * longer than the replay) take the other SMs. Every part of the schedule (a node's last
+ * part, or a parallel segment) is one kernel node whose grid has m CTAs, each reserving
+ * more than half of an SM's shared memory so that the kernel holds m SMs; every
  * CTA runs for C^ ((1 - f) + f / m) ticks of tick_us microseconds (Eq.1 with Amdahl's
  * parallel fraction f = k/64, not rounded). Edges: each DAG edge u -> v makes every part of
  * v wait for u's last part, and a node's segment runs before its residual part; then by
@@ -302,9 +304,10 @@ int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_
  * SM count, the structure variant (ignored by GREEDY), reps >= 1 timed replays after one
  * warm-up; makespan_us[reps] receives each replay's time (CUDA events around the graph
  * launch) and *bound (may be NULL) the bound in ticks: Theorem 1's R(G), or the Greedy
- * baseline for GREEDY. Synchronous; allocates its own graph and stream. Returns
+ * baseline for GREEDY. Synchronous; allocates its own graph and streams. Returns
  * DAGRT_E_INVAL (bad argument, M above the SM count, a part above M SMs), the schedule's
- * per-DAG error, DAGRT_E_DEVICE or DAGRT_E_TIMEOUT (a kernel's wait hit its limit). */
+ * per-DAG error, DAGRT_E_DEVICE, DAGRT_E_TIMEOUT (a kernel's wait hit its limit) or
+ * DAGRT_E_INTERNAL (a replay outlasted the fillers: it may have used more than M SMs). */
 #define DAGRT_REALISE_BARRIER 0
 #define DAGRT_REALISE_EDGES 1
 #define DAGRT_REALISE_GREEDY 2

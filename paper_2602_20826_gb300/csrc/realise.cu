@@ -6,15 +6,18 @@
 // shared memory, so that a CTA holds an SM to itself and a kernel of m CTAs holds m SMs.
 // A load is emulated by time, as the paper emulates it by iteration counts: every CTA of a
 // part with load C^ and parallel fraction f = k/64 on m SMs runs for C^ ((1 - f) + f / m)
-// ticks (Amdahl's law; Eq.1 without rounding). The graph's edges are the DAG's edges (a
-// node's parts wait for its predecessors' last parts; a node's segment runs before its
-// residual part) plus, by mode, the schedule's extra edges of Alg.2 or a barrier between
-// consecutive groups. The measured makespan can then be set against Theorem 1's bound in
-// ticks.
+// ticks (Amdahl's law; Eq.1 without rounding). The GPU is narrowed to the model's M SMs
+// by filler CTAs that hold the other SMs for the length of a replay. The graph's edges are
+// the DAG's edges (a node's parts wait for its predecessors' last parts; a node's segment
+// runs before its residual part) plus, by mode, the schedule's extra edges of Alg.2 or a
+// barrier between consecutive groups. The measured makespan can then be set against
+// Theorem 1's bound in ticks.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <set>
+#include <thread>
 #include <vector>
 
 #include "dagrt.h"
@@ -220,26 +223,47 @@ extern "C" int dagrt_realise(dagrt_ctx *ctx, int32_t V, const int32_t *row_ptr, 
     }
     if (!from.empty() && cudaGraphAddDependencies(gg.g, from.data(), to.data(), nullptr, from.size()) != cudaSuccess)
         return DAGRT_E_DEVICE;
-    cudaStream_t st = nullptr;
+    // an M-SM GPU on this n_sm-SM one: before each replay, n_sm - M filler CTAs (one per SM,
+    // each holding its SM for a fixed time longer than the replay can take) take the other
+    // SMs, so that the graph's kernels find M free SMs. Nothing waits on anything: the
+    // fillers end by their own clock.
+    cudaStream_t st = nullptr, fill = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return DAGRT_E_DEVICE;
+    if (cudaStreamCreateWithFlags(&fill, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamDestroy(st);
+        return DAGRT_E_DEVICE;
+    }
+    const uint64_t fill_ns = (uint64_t)(2.0 * 1e3 * tick_us * (double)(the_bound > 0 ? the_bound : 1)) + 2000000ull;
     int out = DAGRT_OK;
     if (cudaGraphInstantiate(&gg.x, gg.g, 0) != cudaSuccess || cudaEventCreate(&gg.e0) != cudaSuccess ||
         cudaEventCreate(&gg.e1) != cudaSuccess || cudaGraphUpload(gg.x, st) != cudaSuccess)
         out = DAGRT_E_DEVICE;
     for (int r = -1; r < reps && out == DAGRT_OK; r++) {  // one warm-up replay
+        if (n_sm > M) {
+            k_emulate<<<n_sm - M, 32, kRealiseSmem, fill>>>(fill_ns, gg.err);
+            if (cudaGetLastError() != cudaSuccess) {
+                out = DAGRT_E_DEVICE;
+                break;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(300));  // let the fillers take their SMs
+        }
         if (cudaEventRecord(gg.e0, st) != cudaSuccess || cudaGraphLaunch(gg.x, st) != cudaSuccess ||
-            cudaEventRecord(gg.e1, st) != cudaSuccess || cudaEventSynchronize(gg.e1) != cudaSuccess) {
+            cudaEventRecord(gg.e1, st) != cudaSuccess || cudaEventSynchronize(gg.e1) != cudaSuccess ||
+            cudaStreamSynchronize(fill) != cudaSuccess) {
             out = DAGRT_E_DEVICE;
             break;
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, gg.e0, gg.e1);
         if (r >= 0) makespan_us[r] = 1e3f * ms;
+        if (n_sm > M && 1e3 * (double)ms + 300.0 > 1e-3 * (double)fill_ns) out = DAGRT_E_INTERNAL;  // outlived the fillers
     }
     int32_t err = 0;
     if (out == DAGRT_OK && cudaMemcpy(&err, gg.err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess) out = DAGRT_E_DEVICE;
     cudaStreamSynchronize(st);
+    cudaStreamSynchronize(fill);
     cudaStreamDestroy(st);
+    cudaStreamDestroy(fill);
     if (out == DAGRT_OK && err) out = err;
     if (bound) *bound = the_bound;
     return out;
