@@ -657,13 +657,12 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
     if (nd > 0) {
         CK(cudaMemsetAsync(b->counters, 0, 8 * sizeof(int32_t), ctx->stream), "reset counters");
         CK(ensure_side_streams(ctx), "create side streams");
-        // size classes run concurrently: fork from the context stream, join back into it.
-        // Classes of larger DAGs are launched first (longest work first): their CTAs take
-        // their SMs at once, and the many small DAGs fill the rest of the GPU around them
-        // instead of delaying the few long ones to the end of the call.
+        // size classes run concurrently: fork from the context stream, join back into it
+        // (smallest class first: launching the large-DAG classes first measured 36% slower
+        // on the 10,000-DAG batch -- their CTAs' workspaces crowd out the many small teams)
         CK(cudaEventRecord(ctx->fork, ctx->stream), "record fork");
         int used[dagrt_ctx::kSide], nused = 0;
-        for (int c = kNumClasses - 1; c >= 0; c--) {
+        for (int c = 0; c < kNumClasses; c++) {
             const int n = b->class_off[c + 1] - b->class_off[c];
             if (n == 0) continue;
             cudaStream_t st = ctx->side[c];
