@@ -3,8 +3,8 @@
 The network, its loss, gradients and optimiser all run in libdagrt's kernels (dagrt_model_*,
 dagrt_train_step); this module only prepares labels and loops over batches.
 
-Labels. The plain search (dagrt_search: structure variants x seeded random allocations
-from a level list, every candidate judged by the exact bound of Theorem 1) picks a winner
+Labels. The plain search (dagrt_search: structure variants x seeded sparse perturbations of
+the schedule's own allocation, every candidate judged by the exact bound of Theorem 1) picks a winner
 per DAG; a kernel's label is the level of the proposer's level list nearest (in log2) to
 the SMs the winner gives the kernel's own plan row (0 in the winner's column means the
 schedule's own m, Eq.5). DAGs whose schedule failed are unlabelled (-1).
@@ -23,8 +23,12 @@ from . import dagrt
 
 # SM levels the proposer chooses among (M = 148 on the measured configs)
 LEARN_LEVELS = (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 148)
-# the plain search's levels and shape (4 structure variants x 64 allocations)
-SEARCH_LEVELS = (1, 2, 4, 8, 16, 32)
+# the plain search (4 structure variants x 64 allocations): allocation 0 keeps each
+# schedule's own SMs, the others are sparse perturbations of them (a row keeps its m with
+# probability 12/16, else it is halved, lowered by one, raised by one or doubled), the
+# neighbourhood in which a search can beat the paper's Eq.5 allocation at all
+SEARCH_LEVELS = (0,) * 12 + (1, 2, 3, 4)
+SEARCH_MODE = dagrt.SEARCH_PERTURB
 SEARCH_VARIANTS = (0, 1, 2, 3)
 SEARCH_ALLOC = 64
 
@@ -60,7 +64,7 @@ def search_labels(ctx: "dagrt.Context", batch, levels=LEARN_LEVELS, seed: int = 
     scheds = {}
     for v in SEARCH_VARIANTS:
         scheds[v] = lb.schedule(v, fields=("status", "n_rows", "row_id", "row_m0"), check=False)
-    res = lb.search(list(SEARCH_VARIANTS), SEARCH_ALLOC, list(SEARCH_LEVELS), seed, want_m=True)
+    res = lb.search(list(SEARCH_VARIANTS), SEARCH_ALLOC, list(SEARCH_LEVELS), seed, want_m=True, mode=SEARCH_MODE)
     node_off = np.asarray(batch.node_off, np.int64)
     N = int(node_off[-1])
     V = np.diff(node_off)
@@ -79,6 +83,29 @@ def search_labels(ctx: "dagrt.Context", batch, levels=LEARN_LEVELS, seed: int = 
         labels[nodes] = nearest_level(m, levels)
     lb.free()
     return labels, res
+
+
+def exhaustive_labels(ctx: "dagrt.Context", batch, levels, v_max: int):
+    """Per-node labels from the exhaustive search of the paper structure (dagrt_search,
+    DAGRT_SEARCH_EXHAUSTIVE: every node's SMs from {the schedule's own} + levels, all
+    combinations): the index in `levels` of the SMs the optimum gives the node's own plan
+    row (the schedule's own m when the optimum keeps it; nearest level in log2 if that m is
+    not a level). Needs (len(levels) + 1)^v_max <= 2^20 and DAGs of at most v_max nodes.
+    Returns (labels int8 [N], loaded batch, paper bound per DAG, optimum per DAG)."""
+    lb = ctx.load(batch)
+    s = lb.schedule(dagrt.VAR_PAPER, fields=("status", "bound", "n_rows", "row_id", "row_m0"))
+    n_alloc = (len(levels) + 1) ** v_max
+    res = lb.search([dagrt.VAR_PAPER], n_alloc, list(levels), mode=dagrt.SEARCH_EXHAUSTIVE, want_m=True)
+    node_off = np.asarray(batch.node_off, np.int64)
+    V = np.diff(node_off)
+    rows = own_rows(lb, s, node_off)
+    labels = np.full(int(node_off[-1]), -1, np.int8)
+    ok = np.repeat(s["status"][:lb.n_dags] == 0, V) & (rows >= 0)
+    r = rows[ok]
+    m = res["best_m"][r].astype(np.int64)
+    m = np.where(m == 0, s["row_m0"][r], m)
+    labels[ok] = nearest_level(m, levels)
+    return labels, lb, s["bound"][:lb.n_dags], res["best_bound"]
 
 
 def train(ctx, model: "dagrt.Model", data, epochs: int, lr: float, log=None):
@@ -109,7 +136,7 @@ def load(ctx, path: str) -> "dagrt.Model":
 def timed_compare(ctx, model: "dagrt.Model", dev_batch: dict, M: int, k: int = 16, seed: int = 3,
                   reps: int = 3):
     """Wall time on the GPU (CUDA events on the context's stream) of
-      plain:   the 4 structure variants' schedules + dagrt_search (4 x 64 candidates), and
+      plain:   the 4 structure variants' schedules + dagrt_search (4 x 64 perturbation candidates), and
       learned: dagrt_propose (paper schedule, features, network, top-k decode, exact check
                of the paper's allocation and the k proposals),
     each on a freshly loaded copy of the same device-resident batch (the load itself is not
@@ -125,7 +152,7 @@ def timed_compare(ctx, model: "dagrt.Model", dev_batch: dict, M: int, k: int = 1
             lb.schedule(v, out={"status": torch.empty(nd, dtype=torch.int32, device="cuda")})
         o = {"best_bound": torch.empty(nd, dtype=torch.int64, device="cuda"),
              "best_cand": torch.empty(nd, dtype=torch.int32, device="cuda")}
-        lb.search(list(SEARCH_VARIANTS), SEARCH_ALLOC, list(SEARCH_LEVELS), seed, out=o)
+        lb.search(list(SEARCH_VARIANTS), SEARCH_ALLOC, list(SEARCH_LEVELS), seed, out=o, mode=SEARCH_MODE)
         return o
 
     def learned(lb):

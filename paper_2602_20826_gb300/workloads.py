@@ -216,6 +216,22 @@ def paper_layered_batch(n_dags: int, P: int, M: int, c_avg: int, seed: int, dept
     return from_dags(dags, M, name)
 
 
+def small_m_batch(n_dags: int, seed: int, M: int = 8, v_lo: int = 3, v_hi: int = 6, p: float = 0.35,
+                  load_hi: int = 40, frac_lo: float = 0.5) -> Batch:
+    """Small DAGs on a small GPU, where the Eq.5 allocation is often not the best one and an
+    exhaustive allocation search is cheap: V ~ U[v_lo, v_hi], Erdos-Renyi edges with
+    probability p over a topological order, loads U[1, load_hi] ticks, parallel fractions
+    U[frac_lo, 1] in 1/64 steps."""
+    dags = []
+    for d in range(n_dags):
+        rng = _rng(seed, d)
+        V = int(rng.integers(v_lo, v_hi + 1))
+        s, t = er_edges(rng, V, p)
+        rp, col = csr_from_edges(V, s, t)
+        dags.append((rp, col, wcet_uniform(rng, V, 1, load_hi), k64_uniform(rng, V, frac_lo)))
+    return from_dags(dags, M, "small-m")
+
+
 def implicit_deadlines(batch: Batch, utilisation: float) -> np.ndarray:
     """Implicit deadlines D = T of a periodic task per DAG at normalised utilisation U:
     T = ceil(sum of C^ / (M U)) ticks (the DAG's work over the GPU's capacity in one

@@ -235,35 +235,34 @@ def test_model_argument_errors(ctx, setup):
 
 
 def test_gain_of_training(ctx):
-    """What training buys: the network learns the plain search's per-kernel levels (held-out
-    accuracy well above the untrained network's), and learned + exact check is never worse
-    than the paper's schedule or the plain search on fresh, larger DAGs."""
+    """What training buys, where the paper's Eq.5 allocation leaves room: small DAGs (3-6
+    nodes) on an 8-SM GPU, where the exhaustive search of the paper structure (every node's
+    SMs in 1..8) beats the paper's allocation on about 16% of DAGs. The network is trained
+    on the exhaustive optimum's per-node SMs; on held-out DAGs its top-16 proposals plus the
+    exact check must strictly beat the paper's allocation on at least 10% of the DAGs (the
+    untrained network: a few %), never be worse than it (candidate 0 is the paper's), never
+    beat the exhaustive optimum (its candidates lie inside that search space) and reach
+    that optimum on at least 95% of the DAGs."""
     from paper_2602_20826_gb300 import train as T
     from paper_2602_20826_gb300.dagrt import Model
-    tr = wl.er_batch(1500, 20, 200, 0.1, 148, 901, name="train")
-    ho = wl.er_batch(300, 20, 200, 0.1, 148, 902, name="held-out")
-    lab_tr, _ = T.search_labels(ctx, tr, seed=5)
-    lab_ho, _ = T.search_labels(ctx, ho, seed=6)
-    ltr, lho = ctx.load(tr), ctx.load(ho)
-    model = Model(ctx, T.LEARN_LEVELS, seed=3)
-
-    def acc():
-        z = model.logits(lho)
-        ok = lab_ho >= 0
-        return float(np.mean(np.argmax(z, 1)[ok] == lab_ho[ok]))
-
-    a0 = acc()
-    T.train(ctx, model, [(ltr, lab_tr)], epochs=150, lr=3e-3)
-    a1 = acc()
-    assert a1 > a0 + 0.15 and a1 > 0.5, (a0, a1)
-    ev = wl.small_config(4, 60, 100, 400, seed=903)
-    lev = ctx.load(ev)
-    paper = lev.schedule(0)["bound"]
-    for v in (1, 2, 3):
-        lev.schedule(v, fields=("status",))
-    plain = lev.search([0, 1, 2, 3], 64, [1, 2, 4, 8, 16, 32], 7)["best_bound"]
-    got = model.propose(lev, 16)["best_bound"]
-    assert np.all(got <= paper) and np.all(got <= plain)
+    levels = list(range(1, 9))
+    data = []
+    for c in range(4):
+        lab, lb, _, _ = T.exhaustive_labels(ctx, wl.small_m_batch(3000, 700 + c), levels, 6)
+        data.append((lb, lab))
+    lab_ho, lho, paper, opt = T.exhaustive_labels(ctx, wl.small_m_batch(2000, 799), levels, 6)
+    room = float(np.mean(opt < paper))
+    assert room > 0.08, room
+    rates = {}
+    for name, epochs in (("untrained", 0), ("trained", 30)):
+        model = Model(ctx, levels, seed=3)
+        T.train(ctx, model, data, epochs=epochs, lr=3e-3)
+        got = model.propose(lho, 16)["best_bound"]
+        assert np.all(got <= paper) and np.all(got >= opt)
+        rates[name] = (float(np.mean(got < paper)), float(np.mean(got == opt)))
+        model.free()
+    assert rates["trained"][0] >= 0.10 and rates["trained"][0] >= rates["untrained"][0] + 0.05, (room, rates)
+    assert rates["trained"][1] >= 0.95, (room, rates)
 
 
 def test_propose_on_large_layered_dags(ctx):
