@@ -282,6 +282,35 @@ int dagrt_schedule_noalloc(int32_t n_dags, const int64_t *node_off, const int64_
                            const uint8_t *k64, int64_t total_nodes, int64_t total_edges, int32_t M,
                            int32_t variant, int64_t *bound, int32_t *status, void *cuda_stream);
 
+/* ---------------------------------------------------------------- conditional DAGs
+ * The paper names conditional DAGs as future work; this is one reading of them. A node with
+ * cond[v] = 1 takes exactly one of its out-edges per job (the branch its outcome selects).
+ * A node runs when it is a source or one of its in-edges is active; an edge is active when
+ * its tail runs and either is not conditional or chose that edge. A realisation (one choice
+ * per conditional node) is then a plain DAG: the running nodes, renumbered in increasing
+ * order, and the active edges. Choice tuples are enumerated in mixed radix (the lowest-id
+ * conditional node varying fastest), a realisation equal to an earlier one is dropped, and
+ * all realisations of all DAGs are scheduled and bounded (Alg.1, Alg.2 with `variant`,
+ * Theorem 1) in one batched dagrt_schedule call; the worst one is taken on the device.
+ * Inputs: host arrays in dagrt_load_csr's layout plus cond[total_nodes] (uint8 0/1); M;
+ * max_real (1 .. 65536) realisations per DAG at most. Outputs per DAG (host arrays):
+ *   adaptive[n_dags]   the largest bound over the realisations, each scheduled on its own
+ *                      (the schedule chosen when a job's outcomes are known at release);
+ *                      -1 if some realisation failed
+ *   fixed[n_dags]      the bound of the whole DAG with every branch present: one schedule
+ *                      for every job, a branch not taken running for no time (within its C,
+ *                      so the bound holds by Theorem 1's sustainability); may be NULL
+ *   worst_real[n_dags] index of the first realisation attaining `adaptive`; may be NULL
+ *   n_real[n_dags]     number of distinct realisations; may be NULL
+ * Synchronous; allocates its batch and scratch. Returns DAGRT_E_INVAL (bad arguments or
+ * CSR shape), DAGRT_E_RANGE / DAGRT_E_CYCLE (a DAG's edges), DAGRT_E_CAP (more than 2^20
+ * choice tuples or more than max_real realisations in some DAG), a scheduling error, or
+ * DAGRT_E_DEVICE / DAGRT_E_OOM. */
+int dagrt_cond_bound(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, const int64_t *edge_off,
+                     const int32_t *row_ptr, const int32_t *col, const int64_t *wcet, const uint8_t *k64,
+                     const uint8_t *cond, int32_t M, int32_t variant, int32_t max_real, int64_t *adaptive,
+                     int64_t *fixed, int32_t *worst_real, int32_t *n_real);
+
 /* ---------------------------------------------------------------- realisation on the GPU
  * A schedule of one DAG run on this GPU as a CUDA graph, as in the case study of the
  * Evaluation section (CUDA Graph API; m_i realised through the kernel's launch shape; loads
@@ -321,14 +350,14 @@ int dagrt_realise(dagrt_ctx *ctx, int32_t V, const int32_t *row_ptr, const int32
  *   warp_max_v  scheduler: DAGs of at most this many nodes (and at most 12 edges per node
  *               of their class) are scheduled by warp teams in shared memory, larger ones by
  *               CTA teams with global workspaces; one of 0 (CTA teams only), 64, 128, 192,
- *               256. Default 256.
+ *               256. Default 192 (the 193-256-node DAGs of a batch run faster as CTA teams).
  *   chunk_rows  candidate bounds: the plan rows of a DAG are cut into work items of whole
  *               groups (Theorem 1's sum splits at group ends), as many as fit in this many
  *               rows (a longer group alone); 8 .. 256. Default 64.
  *   item_warps  candidate bounds: warps per CTA of the work-item kernel, 1 .. 8. Default 4.
  *   cta_smem    scheduler: k in 1 .. 4 = CTA teams keep their workspace in shared memory
  *               while it takes at most 1/k of a CTA's shared memory (smallest large DAGs
- *               first; k teams then fit per SM), 0 = always in global memory. Default 2. */
+ *               first; k teams then fit per SM), 0 = always in global memory. Default 3. */
 typedef struct {
     int32_t warp_max_v;
     int32_t chunk_rows;

@@ -75,6 +75,8 @@ dagrt_schedule_noalloc = _sig("dagrt_schedule_noalloc", C.c_int,
                               [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int64, C.c_int32,
                                C.c_int32, _vp, _vp, _vp])
 
+dagrt_cond_bound = _sig("dagrt_cond_bound", C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32,
+                                                      C.c_int32, C.c_int32, _vp, _vp, _vp, _vp])
 REALISE_BARRIER, REALISE_EDGES, REALISE_GREEDY = 0, 1, 2
 dagrt_realise = _sig("dagrt_realise", C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32,
                                                 C.c_float, C.c_int32, _vp, C.POINTER(C.c_int64)])
@@ -180,6 +182,21 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def cond_bound(self, batch, cond, variant: int = VAR_PAPER, max_real: int = 4096, M: int | None = None):
+        """dagrt_cond_bound on a workloads.Batch (host arrays) with per-node conditional
+        flags: dict of adaptive, fixed, worst_real, n_real (numpy, one entry per DAG)."""
+        a = {k: np.ascontiguousarray(getattr(batch, k)) for k in ("node_off", "edge_off", "row_ptr", "col", "wcet", "k64")}
+        cd = np.ascontiguousarray(cond, np.uint8)
+        n = batch.n_dags
+        out = {"adaptive": np.zeros(max(n, 1), np.int64), "fixed": np.zeros(max(n, 1), np.int64),
+               "worst_real": np.zeros(max(n, 1), np.int32), "n_real": np.zeros(max(n, 1), np.int32)}
+        self.check(dagrt_cond_bound(self.h, n, _ptr(a["node_off"]), _ptr(a["edge_off"]), _ptr(a["row_ptr"]),
+                                    _ptr(a["col"]) if len(a["col"]) else None, _ptr(a["wcet"]), _ptr(a["k64"]),
+                                    _ptr(cd), int(batch.M if M is None else M), int(variant), int(max_real),
+                                    _ptr(out["adaptive"]), _ptr(out["fixed"]), _ptr(out["worst_real"]),
+                                    _ptr(out["n_real"])))
+        return {k: v[:n] for k, v in out.items()}
 
     def realise(self, row_ptr, col, wcet, k64, M: int, mode: int = REALISE_BARRIER, variant: int = VAR_PAPER,
                 tick_us: float = 20.0, reps: int = 10):

@@ -73,3 +73,25 @@ def test_schedulable_flags_match_oracle(ctx):
                 torch.cuda.synchronize()
                 assert np.array_equal(d_ok.cpu().numpy(), ref) and int(d_n.item()) == int(ref.sum())
         lb.free()
+
+
+def test_conditional_dags_match_oracle(ctx):
+    """dagrt_cond_bound: every realisation of every conditional DAG bounded in one batched
+    call; the adaptive and fixed bounds, the worst realisation and the realisation count
+    against the realisation oracle."""
+    from oracle import conditional as CD
+    from tests.oracle_checks import random_small_dag
+    rng = np.random.default_rng(97)
+    dags, conds = [], []
+    for _ in range(60):
+        V = int(rng.integers(1, 14))
+        dags.append(random_small_dag(rng, V, float(rng.uniform(0.1, 0.5)), int(rng.choice([5, 50, 400])), kmin=16))
+        conds.append((rng.random(V) < 0.3).astype(np.uint8))
+    for M in (3, 16, 148):
+        b = wl.from_dags(dags, M)
+        for variant in (0, 4):
+            got = ctx.cond_bound(b, np.concatenate(conds), variant=variant)
+            for d in range(b.n_dags):
+                rp, col, w, k = b.dag(d)
+                a, f, arg, n = CD.cond_bounds(rp, col, w, k, conds[d], M, variant)
+                assert (got["adaptive"][d], got["fixed"][d], got["worst_real"][d], got["n_real"][d]) == (a, f, arg, n), d
