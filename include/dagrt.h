@@ -167,6 +167,13 @@ typedef struct {
     int64_t *greedy;
     int64_t *greedy_unaware;
     int64_t *graham_para;
+    /* [n_dags] a lower bound of every execution of the schedule, -1 where status != 0: the
+     * longest chain of its parts in G (a node's parts one after another, each edge of G
+     * waiting for its tail's last part) weighted by the parts' times C (Eq.1), or the work
+     * bound ceil(sum of m C over the parts / M) if larger (Sec. 2: path length). The
+     * scheduler checks R(G) >= crit_path for every variant but LITERAL (whose launches can
+     * outrun their group) and reports DAGRT_E_INTERNAL for the DAG if it fails. */
+    int64_t *crit_path;
 } dagrt_schedule_out;
 
 /* Run Alg.1 and Alg.2 with structure variant `variant` on every DAG of the batch, evaluate
@@ -350,14 +357,14 @@ int dagrt_realise(dagrt_ctx *ctx, int32_t V, const int32_t *row_ptr, const int32
  *   warp_max_v  scheduler: DAGs of at most this many nodes (and at most 12 edges per node
  *               of their class) are scheduled by warp teams in shared memory, larger ones by
  *               CTA teams with global workspaces; one of 0 (CTA teams only), 64, 128, 192,
- *               256. Default 192 (the 193-256-node DAGs of a batch run faster as CTA teams).
+ *               256. Default 256.
  *   chunk_rows  candidate bounds: the plan rows of a DAG are cut into work items of whole
  *               groups (Theorem 1's sum splits at group ends), as many as fit in this many
  *               rows (a longer group alone); 8 .. 256. Default 64.
  *   item_warps  candidate bounds: warps per CTA of the work-item kernel, 1 .. 8. Default 4.
  *   cta_smem    scheduler: k in 1 .. 4 = CTA teams keep their workspace in shared memory
  *               while it takes at most 1/k of a CTA's shared memory (smallest large DAGs
- *               first; k teams then fit per SM), 0 = always in global memory. Default 3. */
+ *               first; k teams then fit per SM), 0 = always in global memory. Default 2. */
 typedef struct {
     int32_t warp_max_v;
     int32_t chunk_rows;

@@ -155,6 +155,38 @@ def baselines(row_ptr, col, wcet, k64, M: int):
     return (int(rc), int(out[0]), int(out[1]), int(out[2])) if rc == OK else (int(rc), -1, -1, -1)
 
 
+def crit_path(plan: dict, row_ptr, col, M: int) -> int:
+    """Lower bound of every execution of a schedule: the longest chain of its parts along
+    G's edges (a node's parts one after another; an edge waits for its tail's last part),
+    each part weighted by its Eq.1 time, or the work bound ceil(sum m C / M) if larger."""
+    V = int(plan["V"])
+    own = row_owner(plan)
+    T = [0] * V
+    work = 0
+    for r in range(int(plan["n_rows"])):
+        c = exec_time(int(plan["row_load"][r]), int(plan["row_k"][r]), int(plan["row_m0"][r]), M)
+        T[int(own[r])] += c
+        work += int(plan["row_m0"][r]) * c
+    indeg = [0] * V
+    for e in range(int(row_ptr[V]) if V else 0):
+        indeg[int(col[e])] += 1
+    order = [v for v in range(V) if indeg[v] == 0]
+    best = [0] * V
+    i = 0
+    while i < len(order):
+        u = order[i]
+        i += 1
+        best[u] += T[u]
+        for e in range(int(row_ptr[u]), int(row_ptr[u + 1])):
+            s = int(col[e])
+            best[s] = max(best[s], best[u])
+            indeg[s] -= 1
+            if indeg[s] == 0:
+                order.append(s)
+    path = max(best) if V else 0
+    return max(path, -(-work // M))
+
+
 def bound_plan(plan: dict, M: int, alloc=None, stride: int = 1) -> int:
     """Bound of one allocation (per plan row; 0 = keep the scheduled m) on a fixed
     schedule structure."""

@@ -117,7 +117,7 @@ struct dagrt_batch {
     const uint8_t *k64 = nullptr;
     std::vector<std::pair<void *, size_t>> owned;  // pooled device buffers of the batch
     std::vector<int64_t> h_node_off, h_edge_off;
-    dagrt_tuning tune = {192, kChunkRows, 4, 3};  // the fastest setting on the 10,000-DAG batch
+    dagrt_tuning tune = {256, kChunkRows, 4, 2};
     // size classes: warp classes then the CTA class, lists concatenated
     int32_t *lists = nullptr;
     int32_t *counters = nullptr;
@@ -613,7 +613,7 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
         {o.extra_src, (void **)&dv.extra_src, 4 * (size_t)n_extra_cap},
         {o.extra_dst, (void **)&dv.extra_dst, 4 * (size_t)n_extra_cap},
         {o.greedy, (void **)&dv.greedy, 8 * nd},       {o.greedy_unaware, (void **)&dv.greedy_unaware, 8 * nd},
-        {o.graham_para, (void **)&dv.graham_para, 8 * nd},
+        {o.graham_para, (void **)&dv.graham_para, 8 * nd}, {o.crit_path, (void **)&dv.crit_path, 8 * nd},
     };
     if ((o.seg_parent || o.seg_load || o.seg_m || o.seg_group) &&
         !(o.seg_parent && o.seg_load && o.seg_m && o.seg_group))

@@ -52,6 +52,8 @@ struct Ws {
     uint32_t *rem, *cfull;
     uint16_t *mm;
     int32_t *lst, *tmp;
+    // phase F (after Alg.2): the critical-path lower bound
+    uint64_t *cpT, *cpM;
 };
 
 __host__ __device__ inline int pow2_ceil(int v) {
@@ -125,6 +127,10 @@ __host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec,
     w.lst = (int32_t *)take(4ll * (vc + 1));
     w.tmp = (int32_t *)take(4ll * vc);
     mark();
+    off = x0;
+    w.cpT = (uint64_t *)take(8ll * vc);
+    w.cpM = (uint64_t *)take(8ll * vc);
+    mark();
     if (ws) *ws = w;
     return align_up(end, 128);
 }
@@ -164,6 +170,7 @@ __device__ inline void write_failure(const SchedArgs &a, int d, int code) {
     if (a.o.greedy) a.o.greedy[d] = -1;
     if (a.o.greedy_unaware) a.o.greedy_unaware[d] = -1;
     if (a.o.graham_para) a.o.graham_para[d] = -1;
+    if (a.o.crit_path) a.o.crit_path[d] = -1;
 }
 
 // Greedy + unaware kernel time (baseline of the Evaluation section): the kernel runs on
@@ -693,6 +700,7 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             if (a.o.greedy) a.o.greedy[d] = 0;
             if (a.o.greedy_unaware) a.o.greedy_unaware[d] = 0;
             if (a.o.graham_para) a.o.graham_para[d] = 0;
+            if (a.o.crit_path) a.o.crit_path[d] = 0;
         }
         return;
     }
@@ -1113,6 +1121,48 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         j = j1 + 1;
     }
 
+    // ---- critical-path lower bound of the schedule: the longest chain of its parts in G
+    //      (a node's parts run one after another, and every edge waits for its tail's last
+    //      part), weighted by the parts' times, and the work bound ceil(sum m C / M). Every
+    //      execution of the schedule takes at least this long, so Theorem 1's bound must be
+    //      at least it: a device-side consistency check (for the variants whose groups fit M
+    //      or run in sequence). From the plan rows just written, level by level.
+    uint64_t cp = 0;
+    if (a.o.crit_path && a.plan) {  // uniform over the team
+        if (lead) sc[11] = acc.nrows;
+        for (int v = tm.t; v < V; v += NT) {
+            ws.cpT[v] = 0;
+            ws.cpM[v] = 0;
+        }
+        __threadfence_block();  // the plan rows written by other threads of the team
+        tm.sync();
+        const int nr = sc[11];
+        uint64_t work = 0;
+        for (int r = tm.t; r < nr; r += NT) {
+            const uint4 x = a.plan[g.rbase + r];
+            atomicAdd((unsigned long long *)&ws.cpT[x.w], (unsigned long long)x.y);
+            work += (uint64_t)(x.z & 0xffffu) * x.y;
+        }
+        work = tm.sum(work);
+        tm.sync();
+        for (int l = 0; l < nlev; l++) {
+            const int lb = ws.lvl_off[l], lend = (l + 1 < nlev) ? ws.lvl_off[l + 1] : V;
+            for (int i = lb + tm.t; i < lend; i += NT) {
+                const int v = ws.topo[i];
+                const uint64_t dv = ws.cpT[v] + ws.cpM[v];
+                ws.cpT[v] = dv;
+                for (int e = rp[v]; e < (int)rp[v + 1]; e++)
+                    atomicMax((unsigned long long *)&ws.cpM[col[e]], (unsigned long long)dv);
+            }
+            tm.sync();
+        }
+        uint64_t path = 0;
+        for (int v = tm.t; v < V; v += NT) path = ws.cpT[v] > path ? ws.cpT[v] : path;
+        path = tm.maxu(path);
+        const uint64_t wb = (work + M - 1) / M;
+        cp = path > wb ? path : wb;
+    }
+
     // ---- per-DAG and per-node outputs
     if (lead) {
         // candidate bounds fit 32-bit arithmetic: loads < 2^17 and every group sum of
@@ -1121,6 +1171,9 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         if (a.pflag) a.pflag[d] = (mx < (1ull << 17) && mx * waves * 2ull * (uint64_t)V < (1ull << 31)) ? 1 : 0;
         int code = DAGRT_OK;
         if (acc.err) code = DAGRT_E_INTERNAL;
+        // Theorem 1's bound below a lower bound of every execution: an internal error
+        if (a.o.crit_path && a.plan && g.variant != DAGRT_VAR_LITERAL && acc.bound < cp) code = DAGRT_E_INTERNAL;
+        if (a.o.crit_path) a.o.crit_path[d] = a.plan ? (int64_t)cp : -1;
         else if (g.want_edges && acc.nextra > g.ecap) code = DAGRT_E_CAP;
         const int64_t bnd = code == DAGRT_E_INTERNAL ? -1 : (int64_t)acc.bound;
         a.status[d] = code;

@@ -36,7 +36,7 @@ class dagrt_schedule_out(C.Structure):
         "bound", "status", "n_groups", "n_seg", "n_rows", "n_extra", "level", "wanc", "block_of",
         "group_of", "exec_group", "m", "group_R", "seg_parent", "seg_load", "seg_m", "seg_group",
         "row_id", "row_group", "row_m0", "row_load", "extra_off", "extra_src", "extra_dst",
-        "greedy", "greedy_unaware", "graham_para")]
+        "greedy", "greedy_unaware", "graham_para", "crit_path")]
 
 
 def _sig(name, res, args):
@@ -138,7 +138,7 @@ def _is_device(x):
 # per-node / per-DAG output fields and their dtypes
 _DAG_FIELDS = {"bound": np.int64, "status": np.int32, "n_groups": np.int32, "n_seg": np.int32,
                "n_rows": np.int32, "n_extra": np.int64, "greedy": np.int64, "greedy_unaware": np.int64,
-               "graham_para": np.int64}
+               "graham_para": np.int64, "crit_path": np.int64}
 _NODE_FIELDS = {"level": np.int32, "wanc": np.int64, "block_of": np.int32, "group_of": np.int32,
                 "exec_group": np.int32, "m": np.int32, "group_R": np.int64, "seg_parent": np.int32,
                 "seg_load": np.int64, "seg_m": np.int32, "seg_group": np.int32}

@@ -8,7 +8,7 @@ import oracle
 
 FIELDS = ("bound", "status", "n_groups", "n_seg", "n_rows", "n_extra", "level", "wanc", "block_of",
           "group_of", "exec_group", "m", "group_R", "seg_parent", "seg_load", "seg_m", "seg_group",
-          "row_id", "row_group", "row_m0", "row_load", "greedy", "greedy_unaware", "graham_para")
+          "row_id", "row_group", "row_m0", "row_load", "greedy", "greedy_unaware", "graham_para", "crit_path")
 
 
 def context():
@@ -38,6 +38,9 @@ def compare_dag(batch, res, d, variant=0, edges=True):
         rb, g, u, gr = oracle.baselines(*batch.dag(d), batch.M)
         want = (g, u, gr) if rb == 0 else (-1, -1, -1)
         assert (res["greedy"][d], res["greedy_unaware"][d], res["graham_para"][d]) == want, (d, want)
+    if "crit_path" in res:
+        want = oracle.crit_path(ref, *batch.dag(d)[:2], batch.M) if rc == 0 else -1
+        assert res["crit_path"][d] == want, (d, res["crit_path"][d], want)
     if rc != 0:
         assert res["bound"][d] == -1
         return ref

@@ -486,6 +486,49 @@ def test_structure_on_random_small_dags(var):
         _check_structure(rp, col, w, k, M, var, r)
 
 
+def test_critical_path_lower_bound():
+    """The schedule's critical-path lower bound (oracle.crit_path) against a longest-path DP
+    over the expanded graph (every part a node; a node's parts chained in plan order, i.e.
+    by group; an edge of G from the tail's last part to every part of the head) and the work
+    bound,
+    computed here; it never exceeds R(G) except under the literal Alg.2; on a chain and at
+    M = 1 it equals R(G)."""
+    rng = np.random.default_rng(47)
+    for _ in range(120):
+        V = int(rng.integers(1, 20))
+        M = int(rng.choice([1, 2, 4, 8, 148]))
+        rp, col, w, k = random_small_dag(rng, V, 0.3, 60)
+        succ = succ_lists(rp, col)
+        for var in range(5):
+            rc, r = oracle.schedule(rp, col, w, k, M, var, extra_cap=0)
+            n = r["n_rows"]
+            rid = [int(x) for x in r["row_id"][:n]]
+            own = [x if x < V else int(r["seg_parent"][x - V]) for x in rid]
+            wt = [amdahl_time(int(r["row_load"][i]), int(r["row_k"][i]), int(r["row_m0"][i]), M) for i in range(n)]
+            last = {x: i for i, x in enumerate(rid) if x < V}
+            # a node's parts one after another, in plan order (their groups increase)
+            edges = []
+            for v in range(V):
+                mine = [i for i in range(n) if own[i] == v]
+                edges += list(zip(mine, mine[1:]))
+            edges += [(last[u], i) for u in range(V) for s in succ[u] for i in range(n) if own[i] == s]
+            want = max(longest_weighted_path(n, edges, wt),
+                       -(-sum(int(r["row_m0"][i]) * wt[i] for i in range(n)) // M))
+            got = oracle.crit_path(r, rp, col, M)
+            assert got == want
+            if var != oracle.VAR_LITERAL:
+                assert got <= r["bound"]
+            if M == 1:
+                assert got == r["bound"]
+    for _ in range(20):
+        V = int(rng.integers(1, 12))
+        rp, col = wl.csr_from_edges(V, list(range(V - 1)), list(range(1, V)))
+        w = rng.integers(1, 90, size=V)
+        k = rng.integers(0, 65, size=V).astype(np.uint8)
+        rc, r = oracle.schedule(rp, col, w, k, 7)
+        assert oracle.crit_path(r, rp, col, 7) == r["bound"]
+
+
 def test_bound_monotone_in_load_for_fixed_structure():
     """For a fixed schedule structure and allocation, raising any row's load never
     lowers the bound (Eq.1 is non-decreasing in C^; max and sum are monotone)."""
