@@ -1121,6 +1121,39 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         j = j1 + 1;
     }
 
+    // ---- per-DAG and per-node outputs
+    if (lead) {
+        // candidate bounds fit 32-bit arithmetic: loads < 2^17 and every group sum of
+        // C <= ceil(255/M) * max C^ over at most 2V rows below 2^31
+        const uint64_t waves = (255 + M - 1) / M;
+        if (a.pflag) a.pflag[d] = (mx < (1ull << 17) && mx * waves * 2ull * (uint64_t)V < (1ull << 31)) ? 1 : 0;
+        int code = DAGRT_OK;
+        if (acc.err) code = DAGRT_E_INTERNAL;
+        else if (g.want_edges && acc.nextra > g.ecap) code = DAGRT_E_CAP;
+        const int64_t bnd = code == DAGRT_E_INTERNAL ? -1 : (int64_t)acc.bound;
+        a.status[d] = code;
+        a.bound[d] = bnd;
+        if (a.nrows) a.nrows[d] = acc.nrows;
+        if (a.o.status) a.o.status[d] = code;
+        if (a.o.bound) a.o.bound[d] = bnd;
+        if (a.o.n_groups) a.o.n_groups[d] = G;
+        if (a.o.n_seg) a.o.n_seg[d] = acc.nseg;
+        if (a.o.n_rows) a.o.n_rows[d] = acc.nrows;
+        if (a.o.n_extra) a.o.n_extra[d] = acc.nextra;
+        // baselines: Greedy (sequential, m = min(C^, M)), Greedy + unaware (sequential,
+        // m = C^), Graham_para (unit-load nodes: L + ceil((vol - L) / M), L = nodes on the
+        // longest path)
+        if (a.o.greedy) a.o.greedy[d] = (int64_t)b_greedy;
+        if (a.o.greedy_unaware) a.o.greedy_unaware[d] = (int64_t)b_unaware;
+        if (a.o.graham_para) a.o.graham_para[d] = (int64_t)(nlev + (b_vol - nlev + M - 1) / M);
+    }
+    for (int v = tm.t; v < V; v += NT) {
+        if (a.o.block_of) a.o.block_of[n0 + v] = ws.blk[v];
+        if (a.o.group_of) a.o.group_of[n0 + v] = ws.group_of[v];
+        if (a.o.m) a.o.m[n0 + v] = ws.mm[v];
+    }
+    tm.sync();
+
     // ---- critical-path lower bound of the schedule: the longest chain of its parts in G
     //      (a node's parts run one after another, and every edge waits for its tail's last
     //      part), weighted by the parts' times, and the work bound ceil(sum m C / M). Every
@@ -1129,7 +1162,7 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     //      or run in sequence). From the plan rows just written, level by level.
     uint64_t cp = 0;
     if (a.o.crit_path && a.plan) {  // uniform over the team
-        if (lead) sc[11] = acc.nrows;
+        if (lead) sc[11] = acc.nrows;  // (after the outputs that read ws.mm: phase F overlays it)
         for (int v = tm.t; v < V; v += NT) {
             ws.cpT[v] = 0;
             ws.cpM[v] = 0;
@@ -1163,39 +1196,13 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         cp = path > wb ? path : wb;
     }
 
-    // ---- per-DAG and per-node outputs
-    if (lead) {
-        // candidate bounds fit 32-bit arithmetic: loads < 2^17 and every group sum of
-        // C <= ceil(255/M) * max C^ over at most 2V rows below 2^31
-        const uint64_t waves = (255 + M - 1) / M;
-        if (a.pflag) a.pflag[d] = (mx < (1ull << 17) && mx * waves * 2ull * (uint64_t)V < (1ull << 31)) ? 1 : 0;
-        int code = DAGRT_OK;
-        if (acc.err) code = DAGRT_E_INTERNAL;
+    if (lead && a.o.crit_path) {
+        a.o.crit_path[d] = a.plan ? (int64_t)cp : -1;
         // Theorem 1's bound below a lower bound of every execution: an internal error
-        if (a.o.crit_path && a.plan && g.variant != DAGRT_VAR_LITERAL && acc.bound < cp) code = DAGRT_E_INTERNAL;
-        if (a.o.crit_path) a.o.crit_path[d] = a.plan ? (int64_t)cp : -1;
-        else if (g.want_edges && acc.nextra > g.ecap) code = DAGRT_E_CAP;
-        const int64_t bnd = code == DAGRT_E_INTERNAL ? -1 : (int64_t)acc.bound;
-        a.status[d] = code;
-        a.bound[d] = bnd;
-        if (a.nrows) a.nrows[d] = acc.nrows;
-        if (a.o.status) a.o.status[d] = code;
-        if (a.o.bound) a.o.bound[d] = bnd;
-        if (a.o.n_groups) a.o.n_groups[d] = G;
-        if (a.o.n_seg) a.o.n_seg[d] = acc.nseg;
-        if (a.o.n_rows) a.o.n_rows[d] = acc.nrows;
-        if (a.o.n_extra) a.o.n_extra[d] = acc.nextra;
-        // baselines: Greedy (sequential, m = min(C^, M)), Greedy + unaware (sequential,
-        // m = C^), Graham_para (unit-load nodes: L + ceil((vol - L) / M), L = nodes on the
-        // longest path)
-        if (a.o.greedy) a.o.greedy[d] = (int64_t)b_greedy;
-        if (a.o.greedy_unaware) a.o.greedy_unaware[d] = (int64_t)b_unaware;
-        if (a.o.graham_para) a.o.graham_para[d] = (int64_t)(nlev + (b_vol - nlev + M - 1) / M);
-    }
-    for (int v = tm.t; v < V; v += NT) {
-        if (a.o.block_of) a.o.block_of[n0 + v] = ws.blk[v];
-        if (a.o.group_of) a.o.group_of[n0 + v] = ws.group_of[v];
-        if (a.o.m) a.o.m[n0 + v] = ws.mm[v];
+        if (a.plan && g.variant != DAGRT_VAR_LITERAL && acc.bound < cp && a.status[d] == DAGRT_OK) {
+            write_failure(a, d, DAGRT_E_INTERNAL);
+            a.o.crit_path[d] = (int64_t)cp;
+        }
     }
     tm.sync();
 }
