@@ -835,6 +835,7 @@ extern "C" int dagrt_bound(dagrt_batch *b, int32_t n_variants, const int32_t *va
         ch.counter = (uint32_t *)t;  // the first 256 bytes
         ch.acc = (unsigned long long *)(t + 256);
         ch.warps = b->tune.item_warps;
+        ch.alloc_rows = 2 * b->total_nodes;
     }
     int nl = 0;
     {

@@ -8,8 +8,8 @@
 //
 // Two paths. Materialised candidates in blocks of 64 (n_alloc a multiple of 64) take the
 // balanced work items (k_bound_items + k_bound_finish, below): chunks of whole groups of
-// every plan, one warp per (chunk, 64-candidate block), partial bounds added into
-// per-candidate accumulators. Everything else (generated candidates, other n_alloc) takes
+// every plan, one warp per (chunk, 64-candidate block), its rows staged by 2-D TMA tensor
+// copies, partial bounds added into per-candidate accumulators. Everything else (generated candidates, other n_alloc) takes
 // the tile kernel k_bound_tma: one CTA per DAG; row tiles of the DAG -- the candidate bytes
 // of T rows (one contiguous run of T * cand_stride bytes, or none when the candidates are
 // generated in the kernel) and the T plan rows of every variant in the call -- stream from
@@ -17,6 +17,9 @@
 // so the loads of tile i+1 overlap the evaluation of tile i. Each thread owns 1, 2 or 4
 // adjacent candidates of one variant and keeps their running group states; the argmin over
 // the DAG's candidates is reduced with warp shuffles and shared memory in the same kernel.
+#include <cuda.h>  // CUtensorMap and its encoding enums (header only)
+
+#include <cstring>
 #include <type_traits>
 
 #include "bound.cuh"
@@ -340,16 +343,17 @@ __global__ void __launch_bounds__(kBoundMaxThreads) k_bound_tma(BoundArgs a, int
 }
 
 // ------------------------------------------------------------------ balanced work items
-constexpr int kSubRows = 32;     // plan rows staged per load phase of a work item
+constexpr int kSubRows = 32;      // plan rows staged per load phase of a work item
+// rows of one TMA box of candidate bytes (64 bytes wide): a whole phase, one copy (a short
+// last phase copies rows it does not use; boxes of 8 or 16 rows measured slower)
+constexpr int kBoxRows = kSubRows;
 constexpr int kMaxItemWarps = 8;  // warps per CTA of the work-item kernel: ChunkArgs::warps <= this
-// per warp: two staging buffers (candidate bytes + plan rows) and one {C, m} table
-constexpr int kStageBytes = kSubRows * 64 + kSubRows * 16;
+// per warp: two staging buffers (the candidate bytes of a phase, then its plan rows) and the
+// {C, m} table of the phase's rows; every piece 128-byte aligned
+constexpr int kStageCand = kSubRows * 64;
+constexpr int kStageBytes = kStageCand + kSubRows * 16;
 constexpr int kWarpBytes = 2 * kStageBytes + kSubRows * 9 * 8;
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+static_assert(kStageCand % 128 == 0 && kStageBytes % 128 == 0 && kWarpBytes % 128 == 0, "TMA buffer alignment");
 
 // Chunk starts of every DAG of one plan (one warp per DAG). Chunk 0 starts at row 0; each
 // chunk takes whole groups, as many as fit in chunk_rows rows (at least one group), so a
@@ -581,9 +585,27 @@ __device__ __forceinline__ void group_step(uint32_t start, uint32_t end, uint2 t
         : "r"(start), "r"(end), "r"(ta.x), "r"(ta.y), "r"(tb.x), "r"(tb.y), "r"(M));
 }
 
+// 2-D tensor copy (TMA) of one box of candidate bytes: x = first candidate column (a
+// multiple of 64), y = first allocation row; rows past the end of the tensor read as zero
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_g2s_u32(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // Persistent warps over the work items. Per item: its rows (64 candidate bytes and the plan
-// row each, at most kSubRows per phase) are staged by cp.async -- the next item's first
-// phase is staged while this one computes.
+// row each, at most kSubRows per phase) are staged into one of the warp's two buffers by
+// lane 0 -- a 2-D TMA tensor copy of the candidate bytes and a bulk copy of the plan rows,
+// completing on the buffer's mbarrier -- and the next phase (of this item or the next one)
+// is issued into the other buffer before the current one is evaluated.
 //
 // Items whose DAG's sums fit 32 bits: per phase, lane r handles plan row r -- it builds the
 // row's {C, m} table (m = 0: the schedule's own C and m; m = 1, 2, 4, ..., 128: the 32-bit
@@ -596,20 +618,30 @@ __device__ __forceinline__ void group_step(uint32_t start, uint32_t end, uint2 t
 // arithmetic with exec_time for every byte. Each item adds its 64 partial sums into the
 // DAG's per-candidate 64-bit accumulators (the bound is their sum); k_bound_finish reads
 // them once every item is done. At most 64 registers a thread, so that eight CTAs of four
-// warps fit an SM by registers.
+// warps fit an SM by registers. A copy that does not land within the bounded wait sets
+// DAGRT_E_TIMEOUT; the warp then waits (bounded) for its copies in flight and stops.
 template <bool CHECK_M>
-__global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs a, ChunkArgs ch) {
-    extern __shared__ __align__(128) unsigned char sm[];
+__global__ void __launch_bounds__(kMaxItemWarps * 32, 4)
+    k_bound_items(const __grid_constant__ CUtensorMap tmap, BoundArgs a, ChunkArgs ch) {
+    extern __shared__ unsigned char sm[];
     __shared__ int64_t s_cum[kMaxVariantsPerCall + 1];
+    __shared__ __align__(8) uint64_t s_bar[kMaxItemWarps][2];
     griddep_launch_dependents();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned char *wbase = sm + w * kWarpBytes;
+    // the warps' buffers from a 128-byte boundary (TMA destinations)
+    unsigned char *wbase = sm + (((smem_addr(sm) + 127u) & ~127u) - smem_addr(sm)) + w * kWarpBytes;
+    uint64_t *bar = s_bar[w];
     uint2 *tbuf = (uint2 *)(wbase + 2 * kStageBytes);
     const int nv = a.n_variants, ncb = a.n_alloc / 64, n_cand = nv * a.n_alloc;
     const uint32_t M = (uint32_t)a.M;
     if (threadIdx.x == 0) {
         s_cum[0] = 0;
         for (int v = 0; v < nv; v++) s_cum[v + 1] = s_cum[v] + (int64_t)ch.cpre[v][a.n_dags] * ncb;
+    }
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
     }
     __syncthreads();
     const uint32_t total = (uint32_t)s_cum[nv];
@@ -628,15 +660,29 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs
         cb = (int)(jj - q * (uint32_t)ncb);
         rec = ch.item[vi][q];
     };
-    // rows [g0, g1) of item (vi, cb) into staging buffer b
+    uint32_t parity = 0u;    // bit b: parity of the next wait on buffer b
+    uint32_t inflight = 0u;  // bit b: a copy issued into buffer b and not yet waited for
+    // rows [g0, g1) of item (vi, cb) into staging buffer b (the warp is done reading it): one
+    // 2-D TMA box per kBoxRows rows of the 64 candidate bytes, one bulk copy of the plan rows
     auto stage = [&](int b, int vi, int cb, int g0, int g1) {
-        unsigned char *cbuf = wbase + b * kStageBytes;
-        uint4 *pbuf = (uint4 *)(cbuf + kSubRows * 64);
-        const unsigned char *src = a.m_alloc + (int64_t)vi * a.n_alloc + cb * 64;
-        const int rn = g1 - g0;
-        for (int g = lane; g < rn * 4; g += 32)
-            cp_async16(cbuf + g * 16, src + (int64_t)(g0 + (g >> 2)) * a.stride + (g & 3) * 16);
-        if (lane < rn) cp_async16(pbuf + lane, a.plan[vi] + g0 + lane);
+        inflight |= 1u << b;
+        if (lane == 0) {
+            const int rn = g1 - g0, nb = (rn + kBoxRows - 1) / kBoxRows;
+            const uint32_t dst = smem_addr(wbase + b * kStageBytes);
+            fence_proxy_async();  // the warp's reads of the buffer come before the copy's writes
+            mbar_expect_tx(&bar[b], (uint32_t)(nb * kBoxRows * 64 + rn * 16));
+            const int x = vi * a.n_alloc + cb * 64;
+            for (int i = 0; i < nb; i++) tma_load_2d(dst + i * kBoxRows * 64, &tmap, x, g0 + i * kBoxRows, &bar[b]);
+            bulk_g2s_u32(dst + kSubRows * 64, a.plan[vi] + g0, (uint32_t)(rn * 16), &bar[b]);
+        }
+    };
+    auto wait_buf = [&](int b) -> bool {
+        const bool ok = __all_sync(FULL, mbar_wait(&bar[b], (parity >> b) & 1u));
+        if (ok) {
+            parity ^= 1u << b;
+            inflight &= ~(1u << b);
+        }
+        return ok;
     };
 
     uint32_t j = grab();
@@ -646,12 +692,12 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs
         locate(j, vi, cb, rec);
         stage(0, vi, cb, rec.y, min(rec.z, rec.y + kSubRows));
     }
-    while (j < total) {
+    bool failed = false;
+    while (j < total && !failed) {
         const uint32_t jn = grab();
         int vn = 0, cbn = 0;
         int4 recn = make_int4(0, 0, 0, 0);
         if (jn < total) locate(jn, vn, cbn, recn);
-        bool prefetched = false;
         // the item's phases; FIT: 32-bit table path, else 64-bit sums with exec_time
         auto run_item = [&](auto fitc) {
             constexpr bool FIT = decltype(fitc)::value;
@@ -661,13 +707,16 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs
             uint32_t carry = 1u;  // chunks start at a group start
             for (int g0 = rec.y; g0 < rec.z; g0 += kSubRows) {
                 const int rn = min(kSubRows, rec.z - g0);
-                cp_async_wait_all();
-                __syncwarp();
-                const bool more = g0 + kSubRows < rec.z;
-                if (!more && jn < total) {  // stage the next item while this phase computes
-                    stage(buf ^ 1, vn, cbn, recn.y, min(recn.z, recn.y + kSubRows));
-                    prefetched = true;
+                if (!wait_buf(buf)) {
+                    failed = true;
+                    return;
                 }
+                // the next phase into the other buffer, read completely by the last phase: the
+                // item's next rows, or the first rows of the next item
+                if (g0 + kSubRows < rec.z)
+                    stage(buf ^ 1, vi, cb, g0 + kSubRows, min(rec.z, g0 + 2 * kSubRows));
+                else if (jn < total)
+                    stage(buf ^ 1, vn, cbn, recn.y, min(recn.z, recn.y + kSubRows));
                 const unsigned char *cbuf = wbase + buf * kStageBytes;
                 const uint4 *pbuf = (const uint4 *)(cbuf + kSubRows * 64);
                 if constexpr (FIT) {
@@ -744,8 +793,8 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs
                         }
                     }
                 }
-                __syncwarp();
-                if (more) stage(buf, vi, cb, g0 + kSubRows, min(rec.z, g0 + 2 * kSubRows));
+                __syncwarp();  // the buffer and the table are read
+                buf ^= 1;
             }
             // add the item's partial bounds into its DAG's accumulators (reductions: no wait)
             unsigned long long *acc = ch.acc + (int64_t)rec.x * n_cand + vi * a.n_alloc + cb * 64 + 2 * lane;
@@ -756,14 +805,57 @@ __global__ void __launch_bounds__(kMaxItemWarps * 32, 4) k_bound_items(BoundArgs
             run_item(std::true_type());
         else
             run_item(std::false_type());
-        if (!prefetched && jn < total) stage(buf ^ 1, vn, cbn, recn.y, min(recn.z, recn.y + kSubRows));
         j = jn;
         vi = vn;
         cb = cbn;
         rec = recn;
-        buf ^= 1;
     }
-    cp_async_wait_all();
+    if (failed) {
+        // a copy stalled: report it, and give the copies in flight a bounded chance to land
+        // before the CTA's shared memory is released
+        if (lane == 0) {
+            if (a.err) atomicExch(a.err, DAGRT_E_TIMEOUT);
+            for (int b = 0; b < 2; b++)
+                if ((inflight >> b) & 1u) mbar_wait(&bar[b], (parity >> b) & 1u);
+        }
+        __syncwarp();
+    }
+}
+
+// The candidate bytes as a 2-D tensor of bytes for TMA: `rows` allocation rows of `stride`
+// bytes (a multiple of 16, the base 16-byte aligned: both checked by the API), boxes of 64
+// bytes x kBoxRows rows, no swizzle, zero fill past the last row. cuTensorMapEncodeTiled
+// (host-side encoding only) is taken from the driver through the runtime's entry-point query,
+// so the library links no driver stub.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
+}
+
+static cudaError_t encode_alloc_map(const BoundArgs &a, int64_t rows, CUtensorMap *map) {
+    std::memset(map, 0, sizeof *map);
+    if (rows <= 0) return cudaSuccess;  // no candidate rows: no work item copies any
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dim[2] = {(cuuint64_t)a.stride, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.stride};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)kBoxRows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)a.m_alloc, dim, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cudaStream_t st, int *launches) {
@@ -775,15 +867,17 @@ cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cuda
         // the item counter is zero here: set when the scratch was allocated, and reset by
         // k_bound_finish at the end of every call
         cudaError_t e;
+        CUtensorMap tmap;
+        if ((e = encode_alloc_map(a, ch->alloc_rows, &tmap)) != cudaSuccess) return e;
         const int warps = ch->warps < 1 ? 1 : (ch->warps > kMaxItemWarps ? kMaxItemWarps : ch->warps);
-        const int smem = warps * kWarpBytes;
+        const int smem = warps * kWarpBytes + 128;  // + alignment of the warps' buffers to 128 bytes
         auto kern = a.M < 128 ? k_bound_items<true> : k_bound_items<false>;
         int per_sm = 0;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxItemWarps * kWarpBytes);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxItemWarps * kWarpBytes + 128);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
-        kern<<<per_sm * n_sm, warps * 32, smem, st>>>(a, *ch);
+        kern<<<per_sm * n_sm, warps * 32, smem, st>>>(tmap, a, *ch);
         const int g = a.n_dags < 32 * n_sm ? a.n_dags : 32 * n_sm;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(g);

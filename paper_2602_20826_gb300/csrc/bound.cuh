@@ -95,6 +95,7 @@ struct ChunkArgs {
     uint32_t *counter;            // work-item counter
     unsigned long long *acc;      // [n_dags * n_cand] bound accumulators; zero between calls
     int32_t warps;                // warps per CTA of the work-item kernel
+    int64_t alloc_rows;           // rows of the candidate-byte array (2 * total nodes)
 };
 
 // scratch bytes the balanced path needs for a call (counter, accumulators); all of it must
