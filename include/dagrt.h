@@ -323,7 +323,8 @@ int dagrt_cond_bound(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, co
  * Evaluation section (CUDA Graph API; m_i realised through the kernel's launch shape; loads
  * emulated by one kernel function run for different lengths). The GPU is narrowed to the
  * model's M SMs: before each replay, filler CTAs (one per SM, each running for a fixed time
- * longer than the replay) take the other SMs. Every part of the schedule (a node's last
+ * longer than the replay) take the other SMs, and the graph is launched once every filler
+ * has counted itself in (host-mapped memory). Every part of the schedule (a node's last
  * part, or a parallel segment) is one kernel node whose grid has m CTAs, each reserving
  * more than half of an SM's shared memory so that the kernel holds m SMs; every
  * CTA runs for C^ ((1 - f) + f / m) ticks of tick_us microseconds (Eq.1 with Amdahl's
@@ -342,8 +343,9 @@ int dagrt_cond_bound(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, co
  * launch) and *bound (may be NULL) the bound in ticks: Theorem 1's R(G), or the Greedy
  * baseline for GREEDY. Synchronous; allocates its own graph and streams. Returns
  * DAGRT_E_INVAL (bad argument, M above the SM count, a part above M SMs), the schedule's
- * per-DAG error, DAGRT_E_DEVICE, DAGRT_E_TIMEOUT (a kernel's wait hit its limit) or
- * DAGRT_E_INTERNAL (a replay outlasted the fillers: it may have used more than M SMs). */
+ * per-DAG error, DAGRT_E_DEVICE, DAGRT_E_TIMEOUT (a kernel's wait hit its limit, or the
+ * fillers did not all start within a quarter of their time) or DAGRT_E_INTERNAL (a replay
+ * may have outlasted the fillers: it may have used more than M SMs). */
 #define DAGRT_REALISE_BARRIER 0
 #define DAGRT_REALISE_EDGES 1
 #define DAGRT_REALISE_GREEDY 2

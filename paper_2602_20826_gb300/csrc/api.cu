@@ -63,7 +63,7 @@ struct dagrt_ctx {
     DevicePool pool;
     // side streams: the scheduler's size-class kernels run concurrently, forked from and
     // joined back into `stream` with events
-    static constexpr int kSide = 6;
+    static constexpr int kSide = 18;  // one per scheduler size class
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork = nullptr, join[kSide] = {};
     bool side_ready = false;
@@ -87,11 +87,14 @@ static cudaError_t ensure_side_streams(dagrt_ctx *c) {
 
 namespace {
 
-constexpr int kNumWarpClasses = 4;
-constexpr int kWarpClassCap[kNumWarpClasses] = {64, 128, 192, 256};
+// warp-team size classes by node count: DAGs of 1-16, 17-32, ..., 241-256 nodes, each class
+// with the edge capacity of its densest DAG (finer classes than powers of two keep the
+// workspaces close to the DAGs' sizes, so more teams fit an SM)
+constexpr int kNumWarpClasses = 256 / kWarpClassStep;
 // classes after the warp classes: CTA teams with a shared-memory workspace, then CTA teams
 // with global workspaces
 constexpr int kClsCtaSmem = kNumWarpClasses, kClsCtaGlobal = kNumWarpClasses + 1, kNumClasses = kNumWarpClasses + 2;
+static_assert(dagrt_ctx::kSide >= kNumClasses, "a side stream per size class");
 
 struct Plan {
     bool valid = false;
@@ -120,10 +123,11 @@ struct dagrt_batch {
     dagrt_tuning tune = {256, kChunkRows, 4, 2};
     // size classes: warp classes then the CTA class, lists concatenated
     int32_t *lists = nullptr;
-    int32_t *counters = nullptr;
+    int32_t *counters = nullptr;  // [kNumClasses] work-stealing counters of the size classes
     int class_off[kNumClasses + 1] = {0};
     int max_v = 0, big_vcap = 0, big_ecap = 0, big_grid = 0;
     int smem_vcap = 0, smem_ecap = 0;  // capacity of the shared-memory CTA class
+    int wcap_v[kNumWarpClasses] = {0}, wcap_e[kNumWarpClasses] = {0};  // capacities of the warp classes
     unsigned char *gws = nullptr;  // pooled, gws_cap bytes
     int64_t gws_stride = 0;
     size_t gws_cap = 0;
@@ -297,8 +301,8 @@ static int partition_classes(dagrt_batch *b) {
     dagrt_ctx *ctx = b->ctx;
     const int n_dags = b->n_dags, max_v = b->max_v;
     const std::vector<int64_t> &hn = b->h_node_off, &he = b->h_edge_off;
-    int n_warp = 0;  // warp classes enabled
-    while (n_warp < kNumWarpClasses && kWarpClassCap[n_warp] <= b->tune.warp_max_v) n_warp++;
+    const int wmax = b->tune.warp_max_v;  // warp teams: V <= wmax and E <= kEdgesPerNode * wmax
+    int64_t wecap[kNumWarpClasses] = {0};
     std::vector<int32_t> lists(n_dags);
     std::vector<std::vector<int32_t>> cls(kNumClasses);
     std::vector<int32_t> order(n_dags);
@@ -310,12 +314,13 @@ static int partition_classes(dagrt_batch *b) {
     for (int d : order) {
         const int v = (int)(hn[d + 1] - hn[d]);
         const int64_t ed = he[d + 1] - he[d];
-        int c = 0;
-        while (c < n_warp && (v > kWarpClassCap[c] || ed > (int64_t)kEdgesPerNode * kWarpClassCap[c])) c++;
-        if (c < n_warp)
+        if (v <= wmax && ed <= (int64_t)kEdgesPerNode * wmax) {
+            const int c = v > 0 ? (v - 1) / kWarpClassStep : 0;
             cls[c].push_back(d);
-        else
+            wecap[c] = std::max(wecap[c], ed);
+        } else {
             big.push_back(d);
+        }
     }
     // cta_smem = k: a workspace takes at most 1/k of the shared memory, so k teams fit per SM
     const int64_t limit = b->tune.cta_smem > 0 ? sched_smem_limit() / b->tune.cta_smem : 0;
@@ -351,6 +356,10 @@ static int partition_classes(dagrt_batch *b) {
         off += (int)cls[c].size();
     }
     b->class_off[kNumClasses] = off;
+    for (int c = 0; c < kNumWarpClasses; c++) {
+        b->wcap_v[c] = (c + 1) * kWarpClassStep;
+        b->wcap_e[c] = (int)std::max<int64_t>(wecap[c], 1);
+    }
     b->smem_vcap = sv;
     b->smem_ecap = (int)se;
     b->big_vcap = gv;
@@ -463,7 +472,7 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
 
     b->h_edge_off = he;
     if ((e = batch_alloc(b, &b->lists, n_dags)) != cudaSuccess ||
-        (e = batch_alloc(b, &b->counters, 8)) != cudaSuccess || (e = batch_alloc(b, &b->err, 1)) != cudaSuccess ||
+        (e = batch_alloc(b, &b->counters, kNumClasses)) != cudaSuccess || (e = batch_alloc(b, &b->err, 1)) != cudaSuccess ||
         (e = cudaMemsetAsync(b->err, 0, sizeof(int32_t), ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "allocate class lists"));
     if (int rc = partition_classes(b)) return bail(rc);
@@ -655,7 +664,7 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
     a.plan = p.rows;
     a.o = dv;
     if (nd > 0) {
-        CK(cudaMemsetAsync(b->counters, 0, 8 * sizeof(int32_t), ctx->stream), "reset counters");
+        CK(cudaMemsetAsync(b->counters, 0, kNumClasses * sizeof(int32_t), ctx->stream), "reset counters");
         CK(ensure_side_streams(ctx), "create side streams");
         // size classes run concurrently: fork from the context stream, join back into it
         // (smallest class first: launching the large-DAG classes first measured 36% slower
@@ -671,7 +680,9 @@ extern "C" int dagrt_schedule(dagrt_batch *b, int32_t variant, const dagrt_sched
             a.n_list = n;
             a.counter = b->counters + c;
             if (c < kNumWarpClasses) {
-                CK(sched_launch_warp(kWarpClassCap[c], a, ctx->n_sm, st), "launch scheduler (warp teams)");
+                a.vcap = b->wcap_v[c];
+                a.ecap = b->wcap_e[c];
+                CK(sched_launch_warp(a, ctx->n_sm, st), "launch scheduler (warp teams)");
             } else if (c == kClsCtaSmem) {
                 a.vcap = b->smem_vcap;
                 a.ecap = b->smem_ecap;

@@ -36,10 +36,16 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // One emulated kernel: every CTA keeps its SM for `ns` nanoseconds. The wait ends when the
 // timer has advanced by ns, or after an iteration limit well past that (a timer that
-// stopped would otherwise hold the SM): then the error word is set.
-__global__ void __launch_bounds__(32) k_emulate(uint64_t ns, int32_t *err) {
+// stopped would otherwise hold the SM): then the error word is set. A filler CTA first
+// counts itself in `started` (host-mapped memory), so that the host can launch the graph
+// once every filler holds its SM.
+__global__ void __launch_bounds__(32) k_emulate(uint64_t ns, int32_t *err, int32_t *started) {
     extern __shared__ unsigned char reserve[];  // reserved, not used: one CTA per SM
     if (threadIdx.x != 0) return;
+    if (started) {
+        atomicAdd_system(started, 1);
+        __threadfence_system();
+    }
     const uint64_t t0 = global_ns();
     const uint64_t limit = ns + (1ull << 20);  // each poll takes far more than a nanosecond
     for (uint64_t i = 0; i < limit; i++)
@@ -58,8 +64,10 @@ struct GraphGuard {
     cudaGraphExec_t x = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int32_t *err = nullptr;
+    int32_t *started = nullptr;  // host-mapped counter of filler CTAs that hold their SM
     dagrt_batch *b = nullptr;
     ~GraphGuard() {
+        if (started) cudaFreeHost(started);
         if (x) cudaGraphExecDestroy(x);
         if (g) cudaGraphDestroy(g);
         if (e0) cudaEventDestroy(e0);
@@ -166,19 +174,21 @@ extern "C" int dagrt_realise(dagrt_ctx *ctx, int32_t V, const int32_t *row_ptr, 
         return DAGRT_E_DEVICE;
     std::vector<cudaGraphNode_t> node(n_parts);
     std::vector<uint64_t> ns(n_parts);
-    std::vector<void *> args(2 * n_parts);
+    std::vector<void *> args(3 * n_parts);
+    int32_t *no_count = nullptr;
     for (int i = 0; i < n_parts; i++) {
         const double f = kk[i] / 64.0;
         ns[i] = (uint64_t)std::llround(1e3 * tick_us * (double)load[i] * ((1.0 - f) + f / m[i]));
-        args[2 * i] = &ns[i];
-        args[2 * i + 1] = &gg.err;
+        args[3 * i] = &ns[i];
+        args[3 * i + 1] = &gg.err;
+        args[3 * i + 2] = &no_count;
         cudaKernelNodeParams kp;
         std::memset(&kp, 0, sizeof kp);
         kp.func = (void *)k_emulate;
         kp.gridDim = dim3((unsigned)m[i]);
         kp.blockDim = dim3(32);
         kp.sharedMemBytes = kRealiseSmem;
-        kp.kernelParams = &args[2 * i];
+        kp.kernelParams = &args[3 * i];
         if (cudaGraphAddKernelNode(&node[i], gg.g, nullptr, 0, &kp) != cudaSuccess) return DAGRT_E_DEVICE;
     }
     std::vector<cudaGraphNode_t> from, to;
@@ -225,8 +235,9 @@ extern "C" int dagrt_realise(dagrt_ctx *ctx, int32_t V, const int32_t *row_ptr, 
         return DAGRT_E_DEVICE;
     // an M-SM GPU on this n_sm-SM one: before each replay, n_sm - M filler CTAs (one per SM,
     // each holding its SM for a fixed time longer than the replay can take) take the other
-    // SMs, so that the graph's kernels find M free SMs. Nothing waits on anything: the
-    // fillers end by their own clock.
+    // SMs, so that the graph's kernels find M free SMs. The host launches the graph once
+    // every filler has counted itself in (a bounded poll of host-mapped memory); nothing on
+    // the device waits on anything: the fillers end by their own clock.
     cudaStream_t st = nullptr, fill = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return DAGRT_E_DEVICE;
     if (cudaStreamCreateWithFlags(&fill, cudaStreamNonBlocking) != cudaSuccess) {
@@ -235,17 +246,31 @@ extern "C" int dagrt_realise(dagrt_ctx *ctx, int32_t V, const int32_t *row_ptr, 
     }
     const uint64_t fill_ns = (uint64_t)(2.0 * 1e3 * tick_us * (double)(the_bound > 0 ? the_bound : 1)) + 2000000ull;
     int out = DAGRT_OK;
-    if (cudaGraphInstantiate(&gg.x, gg.g, 0) != cudaSuccess || cudaEventCreate(&gg.e0) != cudaSuccess ||
-        cudaEventCreate(&gg.e1) != cudaSuccess || cudaGraphUpload(gg.x, st) != cudaSuccess)
+    int32_t *d_started = nullptr;
+    if (n_sm > M && (cudaHostAlloc(&gg.started, sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess ||
+                     cudaHostGetDevicePointer((void **)&d_started, gg.started, 0) != cudaSuccess))
+        out = DAGRT_E_DEVICE;
+    if (out == DAGRT_OK && (cudaGraphInstantiate(&gg.x, gg.g, 0) != cudaSuccess || cudaEventCreate(&gg.e0) != cudaSuccess ||
+        cudaEventCreate(&gg.e1) != cudaSuccess || cudaGraphUpload(gg.x, st) != cudaSuccess))
         out = DAGRT_E_DEVICE;
     for (int r = -1; r < reps && out == DAGRT_OK; r++) {  // one warm-up replay
         if (n_sm > M) {
-            k_emulate<<<n_sm - M, 32, kRealiseSmem, fill>>>(fill_ns, gg.err);
+            *(volatile int32_t *)gg.started = 0;
+            k_emulate<<<n_sm - M, 32, kRealiseSmem, fill>>>(fill_ns, gg.err, d_started);
             if (cudaGetLastError() != cudaSuccess) {
                 out = DAGRT_E_DEVICE;
                 break;
             }
-            std::this_thread::sleep_for(std::chrono::microseconds(300));  // let the fillers take their SMs
+            // wait until the fillers hold their SMs (at most a quarter of their time)
+            const auto t0 = std::chrono::steady_clock::now();
+            while (*(volatile int32_t *)gg.started < n_sm - M &&
+                   std::chrono::steady_clock::now() - t0 < std::chrono::nanoseconds(fill_ns / 4))
+                std::this_thread::yield();
+            if (*(volatile int32_t *)gg.started < n_sm - M) {
+                cudaStreamSynchronize(fill);
+                out = DAGRT_E_TIMEOUT;
+                break;
+            }
         }
         if (cudaEventRecord(gg.e0, st) != cudaSuccess || cudaGraphLaunch(gg.x, st) != cudaSuccess ||
             cudaEventRecord(gg.e1, st) != cudaSuccess || cudaEventSynchronize(gg.e1) != cudaSuccess ||
@@ -256,7 +281,8 @@ extern "C" int dagrt_realise(dagrt_ctx *ctx, int32_t V, const int32_t *row_ptr, 
         float ms = 0.f;
         cudaEventElapsedTime(&ms, gg.e0, gg.e1);
         if (r >= 0) makespan_us[r] = 1e3f * ms;
-        if (n_sm > M && 1e3 * (double)ms + 300.0 > 1e-3 * (double)fill_ns) out = DAGRT_E_INTERNAL;  // outlived the fillers
+        if (n_sm > M && 1e3 * (double)ms + 1e-3 * (double)(fill_ns / 4) > 1e-3 * (double)fill_ns)
+            out = DAGRT_E_INTERNAL;  // may have outlived the fillers
     }
     int32_t err = 0;
     if (out == DAGRT_OK && cudaMemcpy(&err, gg.err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess) out = DAGRT_E_DEVICE;

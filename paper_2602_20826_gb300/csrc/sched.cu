@@ -1208,20 +1208,21 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
 }
 
 // ------------------------------------------------------------------ kernels
-template <int VC>
+// Warp teams for small DAGs: kWarpsPerCta teams per CTA, each with a shared-memory workspace
+// sized for (a.vcap, a.ecap), the largest V and E of the launch's size class.
 __global__ void __launch_bounds__(32 * kWarpsPerCta) k_sched_warp(SchedArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     Ws ws;
-    const int64_t bytes = ws_carve(nullptr, VC, kEdgesPerNode * VC, nullptr);
-    ws_carve(smem + warp * bytes, VC, kEdgesPerNode * VC, &ws);
+    const int64_t bytes = ws_carve(nullptr, a.vcap, a.ecap, nullptr);
+    ws_carve(smem + warp * bytes, a.vcap, a.ecap, &ws);
     Team<32> tm{(int)(threadIdx.x & 31), nullptr};
     for (;;) {
         int idx = 0;
         if (tm.t == 0) idx = atomicAdd(a.counter, 1);
         idx = __shfl_sync(FULL, idx, 0);
         if (idx >= a.n_list) break;
-        schedule_one<32>(tm, ws, a, a.list[idx], VC, kEdgesPerNode * VC);
+        schedule_one<32>(tm, ws, a, a.list[idx], a.vcap, a.ecap);
         __syncwarp();
     }
 }
@@ -1248,32 +1249,21 @@ __global__ void __launch_bounds__(NT) k_sched_cta(SchedArgs a) {
 }
 
 // ------------------------------------------------------------------ launchers
-template <int VC>
-static cudaError_t launch_warp(const SchedArgs &a, int n_sm, cudaStream_t st) {
-    const int64_t bytes = ws_carve(nullptr, VC, kEdgesPerNode * VC, nullptr) * kWarpsPerCta;
-    cudaError_t e = cudaFuncSetAttribute(k_sched_warp<VC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+cudaError_t sched_launch_warp(const SchedArgs &a, int n_sm, cudaStream_t st) {
+    const int64_t bytes = ws_carve(nullptr, a.vcap, a.ecap, nullptr) * kWarpsPerCta;
+    if (bytes > sched_smem_limit()) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_sched_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_warp<VC>, 32 * kWarpsPerCta, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_warp, 32 * kWarpsPerCta, bytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = n_sm * per_sm;
     const int need = ceil_div(a.n_list, kWarpsPerCta);
     if (grid > need) grid = need;
     if (grid < 1) return cudaSuccess;
-    k_sched_warp<VC><<<grid, 32 * kWarpsPerCta, bytes, st>>>(a);
+    k_sched_warp<<<grid, 32 * kWarpsPerCta, bytes, st>>>(a);
     return cudaGetLastError();
-}
-
-cudaError_t sched_launch_warp(int vc, const SchedArgs &a, int n_sm, cudaStream_t st) {
-    switch (vc) {
-        case 64: return launch_warp<64>(a, n_sm, st);
-        case 128: return launch_warp<128>(a, n_sm, st);
-        case 192: return launch_warp<192>(a, n_sm, st);
-        case 256: return launch_warp<256>(a, n_sm, st);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 int sched_cta_grid(int n_sm) {

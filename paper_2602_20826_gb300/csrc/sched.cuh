@@ -10,7 +10,8 @@ namespace dagrt {
 
 constexpr int kWarpsPerCta = 2;    // independent warp teams per CTA (small DAGs)
 constexpr int kCtaThreads = 256;   // threads of a CTA team (large DAGs)
-constexpr int kEdgesPerNode = 12;  // edge capacity of a warp-team workspace, per node
+constexpr int kEdgesPerNode = 12;  // warp teams take DAGs of at most this many edges per node of warp_max_v
+constexpr int kWarpClassStep = 16; // node capacities of the warp-team size classes: 16, 32, ..., 256
 
 // Arguments of one scheduling launch. Every pointer is a device pointer.
 struct SchedArgs {
@@ -49,7 +50,8 @@ struct SchedArgs {
 };
 
 int64_t sched_ws_bytes(int vc, int ec);
-cudaError_t sched_launch_warp(int vc, const SchedArgs &a, int n_sm, cudaStream_t st);
+// warp teams: the workspace (a.vcap, a.ecap) of kWarpsPerCta teams must fit sched_smem_limit()
+cudaError_t sched_launch_warp(const SchedArgs &a, int n_sm, cudaStream_t st);
 int sched_cta_grid(int n_sm);
 cudaError_t sched_launch_cta(const SchedArgs &a, int grid, cudaStream_t st);
 // CTA teams with the workspace (a.vcap, a.ecap) in shared memory: sched_ws_bytes of the
