@@ -72,7 +72,34 @@ struct dagrt_ctx {
     int64_t capture_launch0 = 0;
     cudaStream_t cap_stream = nullptr;  // captures run here; `stream` is restored at the end
     cudaStream_t saved_stream = nullptr;
+    // pinned host staging of dagrt_load_csr (offsets down, class lists up); pin_ev marks the
+    // end of the last asynchronous copy out of it, waited for before the next reuse
+    void *pin = nullptr;
+    size_t pin_cap = 0;
+    cudaEvent_t pin_ev = nullptr;
+    bool pin_pending = false;
 };
+
+// The context's pinned staging buffer, at least `bytes` long, once its last asynchronous
+// copy has completed.
+static cudaError_t pinned(dagrt_ctx *c, size_t bytes, void **p) {
+    cudaError_t e = cudaSuccess;
+    if (c->pin_pending) {
+        if ((e = cudaEventSynchronize(c->pin_ev)) != cudaSuccess) return e;
+        c->pin_pending = false;
+    }
+    if (!c->pin_ev && (e = cudaEventCreateWithFlags(&c->pin_ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if (bytes > c->pin_cap) {
+        if (c->pin) cudaFreeHost(c->pin);
+        c->pin = nullptr;
+        c->pin_cap = 0;
+        const size_t cap = std::max<size_t>(bytes, 1 << 16);
+        if ((e = cudaHostAlloc(&c->pin, cap, cudaHostAllocDefault)) != cudaSuccess) return e;
+        c->pin_cap = cap;
+    }
+    *p = c->pin;
+    return cudaSuccess;
+}
 
 static cudaError_t ensure_side_streams(dagrt_ctx *c) {
     if (c->side_ready) return cudaSuccess;
@@ -256,6 +283,8 @@ static void ctx_release(dagrt_ctx *ctx) {
         cudaEventDestroy(ctx->fork);
     }
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->pin_ev) cudaEventDestroy(ctx->pin_ev);
+    if (ctx->pin) cudaFreeHost(ctx->pin);
     delete ctx;
 }
 
@@ -303,25 +332,25 @@ static int partition_classes(dagrt_batch *b) {
     const std::vector<int64_t> &hn = b->h_node_off, &he = b->h_edge_off;
     const int wmax = b->tune.warp_max_v;  // warp teams: V <= wmax and E <= kEdgesPerNode * wmax
     int64_t wecap[kNumWarpClasses] = {0};
-    std::vector<int32_t> lists(n_dags);
-    std::vector<std::vector<int32_t>> cls(kNumClasses);
-    std::vector<int32_t> order(n_dags);
-    std::vector<int32_t> cnt(max_v + 2, 0);  // counting sort by descending V
-    for (int d = 0; d < n_dags; d++) cnt[max_v - (int)(hn[d + 1] - hn[d])]++;
-    for (int i = 1; i < (int)cnt.size(); i++) cnt[i] += cnt[i - 1];
-    for (int d = n_dags - 1; d >= 0; d--) order[--cnt[max_v - (int)(hn[d + 1] - hn[d])]] = d;
-    std::vector<int32_t> big;  // CTA-team DAGs, descending V
-    for (int d : order) {
+    int count[kNumClasses] = {0};
+    // sequential passes over the offsets: warp-class DAGs are bucketed by V (their class is
+    // a function of V), CTA-team DAGs listed apart and sorted by descending V
+    std::vector<int32_t> cnt_v(max_v + 2, 0);
+    std::vector<int32_t> big;  // CTA-team DAGs
+    for (int d = 0; d < n_dags; d++) {
         const int v = (int)(hn[d + 1] - hn[d]);
         const int64_t ed = he[d + 1] - he[d];
         if (v <= wmax && ed <= (int64_t)kEdgesPerNode * wmax) {
             const int c = v > 0 ? (v - 1) / kWarpClassStep : 0;
-            cls[c].push_back(d);
+            cnt_v[v]++;
+            count[c]++;
             wecap[c] = std::max(wecap[c], ed);
         } else {
             big.push_back(d);
         }
     }
+    std::stable_sort(big.begin(), big.end(),
+                     [&](int x, int y) { return hn[x + 1] - hn[x] > hn[y + 1] - hn[y]; });  // descending V
     // cta_smem = k: a workspace takes at most 1/k of the shared memory, so k teams fit per SM
     const int64_t limit = b->tune.cta_smem > 0 ? sched_smem_limit() / b->tune.cta_smem : 0;
     int sv = 0, gv = 0;
@@ -339,23 +368,39 @@ static int partition_classes(dagrt_batch *b) {
             in_smem[i] = 1;
         }
     }
+    std::vector<int32_t> big_cls(big.size());
     for (size_t i = 0; i < big.size(); i++) {
         const int d = big[i];
-        if (in_smem[i]) {
-            cls[kClsCtaSmem].push_back(d);
-        } else {
-            cls[kClsCtaGlobal].push_back(d);
+        const int c = in_smem[i] ? kClsCtaSmem : kClsCtaGlobal;
+        big_cls[i] = c;
+        count[c]++;
+        if (!in_smem[i]) {
             gv = std::max(gv, (int)(hn[d + 1] - hn[d]));
             ge = std::max(ge, he[d + 1] - he[d]);
         }
     }
-    int off = 0;
+    // the class lists, each in descending V (equal V: ascending DAG id), in pinned memory
+    int off = 0, pos[kNumClasses];
     for (int c = 0; c < kNumClasses; c++) {
-        b->class_off[c] = off;
-        std::copy(cls[c].begin(), cls[c].end(), lists.begin() + off);
-        off += (int)cls[c].size();
+        b->class_off[c] = pos[c] = off;
+        off += count[c];
     }
     b->class_off[kNumClasses] = off;
+    std::vector<int32_t> start_v(max_v + 2, 0);  // next list slot of each node count
+    for (int c = 0; c < kNumWarpClasses; c++) {
+        int p = b->class_off[c];
+        for (int v = std::min(max_v, (c + 1) * kWarpClassStep); v >= c * kWarpClassStep + (c == 0 ? 0 : 1); v--) {
+            start_v[v] = p;
+            p += cnt_v[v];
+        }
+    }
+    int32_t *lists = nullptr;
+    CK(pinned(ctx, 4 * (size_t)std::max(n_dags, 1), (void **)&lists), "pinned staging");
+    for (int d = 0; d < n_dags; d++) {
+        const int v = (int)(hn[d + 1] - hn[d]);
+        if (v <= wmax && he[d + 1] - he[d] <= (int64_t)kEdgesPerNode * wmax) lists[start_v[v]++] = d;
+    }
+    for (size_t i = 0; i < big.size(); i++) lists[pos[big_cls[i]]++] = big[i];
     for (int c = 0; c < kNumWarpClasses; c++) {
         b->wcap_v[c] = (c + 1) * kWarpClassStep;
         b->wcap_e[c] = (int)std::max<int64_t>(wecap[c], 1);
@@ -364,8 +409,11 @@ static int partition_classes(dagrt_batch *b) {
     b->smem_ecap = (int)se;
     b->big_vcap = gv;
     b->big_ecap = (int)ge;
-    if (n_dags > 0)
-        CK(cudaMemcpyAsync(b->lists, lists.data(), 4 * n_dags, cudaMemcpyHostToDevice, ctx->stream), "copy class lists");
+    if (n_dags > 0) {
+        CK(cudaMemcpyAsync(b->lists, lists, 4 * n_dags, cudaMemcpyHostToDevice, ctx->stream), "copy class lists");
+        CK(cudaEventRecord(ctx->pin_ev, ctx->stream), "record staging event");
+        ctx->pin_pending = true;
+    }
     const int n_big = b->class_off[kClsCtaGlobal + 1] - b->class_off[kClsCtaGlobal];
     if (n_big > 0) {
         b->big_grid = std::min(sched_cta_grid(ctx->n_sm), n_big);
@@ -381,8 +429,6 @@ static int partition_classes(dagrt_batch *b) {
             b->gws_cap = (need + 255) / 256 * 256;
         }
     }
-    // the lists upload reads `lists` asynchronously: wait before it goes out of scope
-    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     return DAGRT_OK;
 }
 
@@ -402,12 +448,15 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
 
     std::vector<int64_t> hn(n_dags + 1), he(n_dags + 1);
-    if (dev) {
-        CK(cudaMemcpyAsync(hn.data(), node_off, sizeof(int64_t) * (n_dags + 1), cudaMemcpyDeviceToHost, ctx->stream),
-           "copy node_off");
-        CK(cudaMemcpyAsync(he.data(), edge_off, sizeof(int64_t) * (n_dags + 1), cudaMemcpyDeviceToHost, ctx->stream),
-           "copy edge_off");
+    if (dev) {  // through the pinned staging buffer
+        int64_t *pin = nullptr;
+        const size_t nb = sizeof(int64_t) * (n_dags + 1);
+        CK(pinned(ctx, 2 * nb, (void **)&pin), "pinned staging");
+        CK(cudaMemcpyAsync(pin, node_off, nb, cudaMemcpyDeviceToHost, ctx->stream), "copy node_off");
+        CK(cudaMemcpyAsync(pin + n_dags + 1, edge_off, nb, cudaMemcpyDeviceToHost, ctx->stream), "copy edge_off");
         CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+        std::memcpy(hn.data(), pin, nb);
+        std::memcpy(he.data(), pin + n_dags + 1, nb);
     } else {
         std::memcpy(hn.data(), node_off, sizeof(int64_t) * (n_dags + 1));
         std::memcpy(he.data(), edge_off, sizeof(int64_t) * (n_dags + 1));
@@ -432,7 +481,7 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
     b->total_nodes = tn;
     b->total_edges = te;
     b->max_v = max_v;
-    b->h_node_off = hn;
+    b->h_node_off = std::move(hn);
     auto bail = [&](int code) {
         batch_release(b);
         delete b;
@@ -455,8 +504,8 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
             (e = batch_alloc(b, &dw, tn)) != cudaSuccess || (e = batch_alloc(b, &dk, tn)) != cudaSuccess)
             return bail(cuda_fail(ctx, e, "allocate batch copy"));
         cudaStream_t st = ctx->stream;
-        if ((e = cudaMemcpyAsync(dn, hn.data(), 8 * (n_dags + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(de, he.data(), 8 * (n_dags + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        if ((e = cudaMemcpyAsync(dn, node_off, 8 * (n_dags + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(de, edge_off, 8 * (n_dags + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(dr, row_ptr, 4 * (tn + n_dags), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
             (te > 0 && (e = cudaMemcpyAsync(dc, col, 4 * te, cudaMemcpyHostToDevice, st)) != cudaSuccess) ||
             (e = cudaMemcpyAsync(dw, wcet, 8 * tn, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
@@ -470,7 +519,7 @@ int dagrt_load_csr(dagrt_ctx *ctx, int32_t n_dags, const int64_t *node_off, cons
         b->k64 = dk;
     }
 
-    b->h_edge_off = he;
+    b->h_edge_off = std::move(he);
     if ((e = batch_alloc(b, &b->lists, n_dags)) != cudaSuccess ||
         (e = batch_alloc(b, &b->counters, kNumClasses)) != cudaSuccess || (e = batch_alloc(b, &b->err, 1)) != cudaSuccess ||
         (e = cudaMemsetAsync(b->err, 0, sizeof(int32_t), ctx->stream)) != cudaSuccess)
