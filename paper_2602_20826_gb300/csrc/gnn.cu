@@ -288,7 +288,8 @@ __device__ __forceinline__ uint2 pack4(const float *f) {
 // unrolled by 4 so that several neighbour rows are in flight per lane (the gather is
 // latency-bound: neighbours are scattered over the DAG). One thread then issues the
 // tcgen05 MMA chain against the resident W^T; the epilogue (bias, ReLU, bf16) reads TMEM with
-// the first 16 warps: warp w takes TMEM lanes 32 (w % 4) .. + 31 and columns 32 (w / 4) .. + 31.
+// the first 16 warps: warp w takes TMEM lanes 32 (w % 4) .. + 31 and columns 32 (w / 4) .. + 31,
+// while the other 16 warps already gather their rows of the next tile.
 constexpr int kFwdWarps = 32;
 
 __device__ __forceinline__ void acc8(float *a, uint4 u) {
@@ -417,9 +418,12 @@ __global__ void __launch_bounds__(32 * kFwdWarps) k_gnn_fwd(GnnGraph g, const ui
         } else if (!ok && t == 0 && err) {
             atomicExch(err, DAGRT_E_TIMEOUT);
         }
+        // no barrier here: the warps without epilogue work start gathering the next tile
+        // (the MMA that read the A tile has completed); the barrier after that gather orders
+        // this epilogue's TMEM reads before the next MMA writes the accumulator
         tmem_fence_before();
-        __syncthreads();
     }
+    __syncthreads();  // every epilogue has read TMEM before it is released
     if (w == 0) tmem_dealloc(taddr, 128);
 }
 
@@ -746,9 +750,12 @@ __global__ void __launch_bounds__(128) k_gnn_bwd_da(GnnGraph g, const uint16_t *
         } else if (t == 0 && err) {
             atomicExch(err, DAGRT_E_TIMEOUT);
         }
+        // no barrier here: each thread goes on to its row of the next dZ tile (the MMA that
+        // read this one has completed); the barrier after that fill orders these TMEM reads
+        // before the next MMA
         tmem_fence_before();
-        __syncthreads();
     }
+    __syncthreads();  // every thread has read TMEM before it is released
     if (w == 0) tmem_dealloc(taddr, S * 128 <= 128 ? 128 : 512);
 }
 
