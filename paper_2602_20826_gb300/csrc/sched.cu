@@ -45,6 +45,7 @@ struct Ws {
     uint64_t *bigk;
     uint16_t *rnd;
     int32_t *thr, *ovl;  // per over-full block: rank of its M-th head; list of over-full blocks
+    uint16_t *fr0, *fr1; // the heads of the current round and of the next one (Alg.1)
     // phase D
     uint16_t *gtmp;
     int32_t *gfill;
@@ -115,6 +116,8 @@ __host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec,
     w.rnd = (uint16_t *)take(2ll * vc);
     w.thr = (int32_t *)take(4ll * (vc + 1));
     w.ovl = (int32_t *)take(4ll * (vc + 1));
+    w.fr0 = (uint16_t *)take(2ll * vc);
+    w.fr1 = (uint16_t *)take(2ll * vc);
     mark();
     off = x0;
     w.gtmp = (uint16_t *)take(2ll * vc);
@@ -880,6 +883,10 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         ws.nround[b] = 0;
         ws.bigk[b] = 0;
     }
+    if (lead) {  // head counts of the current and the next round (sc[12 + (round & 1)])
+        sc[12] = 0;
+        sc[13] = 0;
+    }
     tm.sync();
     // a block of more than M nodes may have more than M heads in a round (Top_M below)
     bool bigblk = false;
@@ -915,38 +922,39 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     for (int v = tm.t; v < V; v += NT) {
         if (ws.cnt[v] > 1) bad = true;
         ws.st[v] = (uint8_t)((ws.st[v] & ST_JOIN) | (ws.cnt[v] == 0 ? ST_ACTIVE : 0));
+        if (ws.cnt[v] == 0) ws.fr0[atomicAdd((int *)&sc[12], 1)] = (uint16_t)v;  // the first heads
     }
     if (tm.any(bad)) {
         if (lead) write_failure(a, d, DAGRT_E_INTERNAL);
         return;
     }
     tm.sync();
+    // Each round works on the list of its heads only (the nodes marked ST_ACTIVE): the heads
+    // that are not selected stay, and a selected node's in-block successor (it has no other
+    // in-block predecessor) becomes a head of the next round.
+    if (lead) sc[10] = 0;
+    tm.sync();
     for (int round = 0;; round++) {
+        const int cur = 12 + (round & 1), nxt = 12 + ((round + 1) & 1);
+        const int nf = sc[cur];
+        if (nf == 0) break;
         if (round > V) {  // every round selects a node, so this cannot happen
             if (lead) write_failure(a, d, DAGRT_E_INTERNAL);
             return;
         }
-        bool act = false;
-        if (lead) sc[10] = 0;
-        for (int v = tm.t; v < V; v += NT)
-            if (ws.st[v] & ST_ACTIVE) {
-                act = true;
-                atomicAdd(&ws.fcnt[ws.blk[v]], 1);
-            }
-        if (!tm.any(act)) break;
+        const uint16_t *F = (round & 1) ? ws.fr1 : ws.fr0;
+        uint16_t *Fn = (round & 1) ? ws.fr0 : ws.fr1;
+        // heads per block; a block with more heads than SMs (only in a block of more than M
+        // nodes) is listed once, by the head that takes its count past M
+        for (int i = tm.t; i < nf; i += NT) {
+            const int b = ws.blk[F[i]];
+            if (atomicAdd(&ws.fcnt[b], 1) == (int)M && bigblk) ws.ovl[atomicAdd((int *)&sc[10], 1)] = b;
+        }
         tm.sync();
-        bool over = false;  // a block with more than M heads (only in a block of more than M nodes)
-        if (bigblk)
-            for (int b = tm.t; b <= N; b += NT) over |= ws.fcnt[b] > (int)M;
-        over = bigblk && tm.any(over);
-        // blocks with more heads than SMs keep their M heaviest (Top_M): list them, then
-        // one warp per such block walks the nodes in rank order (W^anc descending) with
-        // ballots until its M-th active head; the heads up to that rank form Top_M
-        if (over)
-            for (int b = tm.t; b <= N; b += NT)
-                if (ws.fcnt[b] > (int)M) ws.ovl[atomicAdd((int *)&sc[10], 1)] = b;
-        if (over) tm.sync();
-        const int nov = over ? sc[10] : 0;
+        const int nov = sc[10];
+        // blocks with more heads than SMs keep their M heaviest (Top_M): one warp per such
+        // block walks the nodes in rank order (W^anc descending) with ballots until its M-th
+        // head; the heads up to that rank form Top_M
         for (int q = tm.warp(); q < nov; q += NT / 32) {
             const int b = ws.ovl[q];
             int cnt = 0, th = V;
@@ -969,9 +977,10 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             }
             if (tm.lane() == 0) ws.thr[b] = th;
         }
-        if (over) tm.sync();
-        for (int v = tm.t; v < V; v += NT) {
-            if (!(ws.st[v] & ST_ACTIVE)) continue;
+        if (nov) tm.sync();
+        if (lead) sc[cur] = 0;  // read by every thread above: it counts the round after next
+        for (int i = tm.t; i < nf; i += NT) {
+            const int v = F[i];
             const int b = ws.blk[v];
             const bool inT = ws.fcnt[b] <= (int)M || (int)ws.rank[v] <= ws.thr[b];
             if (inT) {
@@ -982,35 +991,41 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
             }
         }
         tm.sync();
-        for (int v = tm.t; v < V; v += NT) {
+        for (int i = tm.t; i < nf; i += NT) {
+            const int v = F[i];
             const uint8_t s0 = ws.st[v];
-            if (!(s0 & ST_INT)) continue;
-            const int b = ws.blk[v];
-            const uint64_t bg = ws.bigk[b];
-            const bool sel = bg == 0 || (int)(bg & 0xffff) == (int)(0xffffu - ws.rank[v]);
+            bool sel = false;
+            if (s0 & ST_INT) {
+                const uint64_t bg = ws.bigk[ws.blk[v]];
+                sel = bg == 0 || (int)(bg & 0xffff) == (int)(0xffffu - ws.rank[v]);
+            }
             if (sel) {
                 ws.st[v] = (uint8_t)((s0 & ~(ST_INT | ST_ACTIVE)) | ST_SEL);
                 ws.rnd[v] = (uint16_t)round;
-                atomicMax(&ws.nround[b], round + 1);
-            } else {
+                atomicMax(&ws.nround[ws.blk[v]], round + 1);
+            } else {  // still a head next round
                 ws.st[v] = (uint8_t)(s0 & ~ST_INT);
+                Fn[atomicAdd((int *)&sc[nxt], 1)] = (uint16_t)v;
             }
         }
         tm.sync();
-        for (int v = tm.t; v < V; v += NT) {
+        for (int i = tm.t; i < nf; i += NT) {
+            const int v = F[i];
             const uint8_t s0 = ws.st[v];
-            if (s0 & (ST_ACTIVE | ST_SEL)) {
-                ws.fcnt[ws.blk[v]] = 0;
-                ws.bigk[ws.blk[v]] = 0;
-            }
+            ws.fcnt[ws.blk[v]] = 0;
+            ws.bigk[ws.blk[v]] = 0;
             if (s0 & ST_SEL) {
                 ws.st[v] = (uint8_t)(s0 & ~ST_SEL);
                 for (int e = rp[v]; e < rp[v + 1]; e++) {
-                    const int s = col[e];
-                    if (ws.blk[s] == ws.blk[v]) ws.st[s] |= ST_ACTIVE;
+                    const int s2 = col[e];
+                    if (ws.blk[s2] == ws.blk[v]) {
+                        ws.st[s2] |= ST_ACTIVE;
+                        Fn[atomicAdd((int *)&sc[nxt], 1)] = (uint16_t)s2;
+                    }
                 }
             }
         }
+        if (lead) sc[10] = 0;
         tm.sync();
     }
     // group index = groups of earlier blocks + round within the block
