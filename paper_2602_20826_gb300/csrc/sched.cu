@@ -46,6 +46,8 @@ struct Ws {
     uint16_t *rnd;
     int32_t *thr, *ovl;  // per over-full block: rank of its M-th head; list of over-full blocks
     uint16_t *fr0, *fr1; // the heads of the current round and of the next one (Alg.1)
+    uint64_t *hmask;     // CTA teams, Top_M of an over-full block: its heads by rank, one bit each
+    int32_t *hcnt;       // ... and the heads in rank words 0..w
     // phase D
     uint16_t *gtmp;
     int32_t *gfill;
@@ -118,6 +120,8 @@ __host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec,
     w.ovl = (int32_t *)take(4ll * (vc + 1));
     w.fr0 = (uint16_t *)take(2ll * vc);
     w.fr1 = (uint16_t *)take(2ll * vc);
+    w.hmask = (uint64_t *)take(8ll * W);
+    w.hcnt = (int32_t *)take(4ll * W);
     mark();
     off = x0;
     w.gtmp = (uint16_t *)take(2ll * vc);
@@ -952,10 +956,39 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         }
         tm.sync();
         const int nov = sc[10];
-        // blocks with more heads than SMs keep their M heaviest (Top_M): one warp per such
-        // block walks the nodes in rank order (W^anc descending) with ballots until its M-th
-        // head; the heads up to that rank form Top_M
-        for (int q = tm.warp(); q < nov; q += NT / 32) {
+        // blocks with more heads than SMs keep their M heaviest (Top_M): the heads up to the
+        // rank of the block's M-th head (rank order = W^anc descending). A CTA team finds it
+        // for a few such blocks from a bit mask of the block's heads over the ranks (a
+        // popcount scan over V/64 words); otherwise one warp per block walks the nodes in rank
+        // order with ballots until its M-th head.
+        bool masked = false;
+        if constexpr (NT > 32) {
+            masked = nov > 0 && nov <= 2;
+            for (int q = 0; masked && q < nov; q++) {
+                const int b = ws.ovl[q];
+                for (int w2 = tm.t; w2 < W; w2 += NT) ws.hmask[w2] = 0;
+                tm.sync();
+                for (int i = tm.t; i < nf; i += NT) {
+                    const int v = F[i];
+                    if (ws.blk[v] == b)
+                        atomicOr((unsigned long long *)&ws.hmask[ws.rank[v] >> 6], 1ull << (ws.rank[v] & 63));
+                }
+                tm.sync();
+                for (int w2 = tm.t; w2 < W; w2 += NT) ws.hcnt[w2] = __popcll(ws.hmask[w2]);
+                tm.sync();
+                team_scan_inplace(tm, ws.hcnt, W, [](uint64_t x, uint64_t y) { return x + y; }, false);
+                for (int w2 = tm.t; w2 < W; w2 += NT) {
+                    uint64_t mk = ws.hmask[w2];
+                    const int upto = ws.hcnt[w2], before = upto - __popcll(mk);
+                    if (before < (int)M && (int)M <= upto) {  // the M-th head is in this word
+                        for (int i = 1; i < (int)M - before; i++) mk &= mk - 1;
+                        ws.thr[b] = w2 * 64 + __ffsll((long long)mk) - 1;
+                    }
+                }
+                tm.sync();
+            }
+        }
+        for (int q = tm.warp(); !masked && q < nov; q += NT / 32) {
             const int b = ws.ovl[q];
             int cnt = 0, th = V;
             for (int base = 0; base < V; base += 32) {
