@@ -476,13 +476,18 @@ def run_cfg5(args):
         lb.schedule(0, out=out)
         lb.free()
 
-    step()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > L2 (129 MB)
+    warm = max(3, args.warmup)
+    for _ in range(warm):
+        flush.zero_()
+        step()
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     l0 = ctx.launches()
     evs = [(E(), E()) for _ in range(steps)]
     for e0, e1 in evs:
+        flush.zero_()
         e0.record(stream)
         step()
         e1.record(stream)
@@ -517,12 +522,13 @@ def run_cfg5(args):
     cpu_v = ns / (time.perf_counter() - ts)
     peak, kind = _peaks()
     alg = b.input_bytes() + 12 * nd
-    line = {"metric": METRIC, "value": nd / t, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": 1,
+    line = {"metric": METRIC, "value": nd / t, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": "config 5: 200 layered DAGs, 2,000-20,000 nodes, depth 20-60, widths 1-64 "
                                    "scaled to V, skip edges p=0.02, lognormal WCET, M=148",
-                       "n_dags": nd, "nodes": b.total_nodes(), "edges": b.total_edges()},
+                       "n_dags": nd, "nodes": b.total_nodes(), "edges": b.total_edges(),
+                       "l2": "flushed between steps (256 MB write)"},
             "propose_top16_ms": float(np.median(pt)), "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / t / 1e9 / peak, "traffic": None,
