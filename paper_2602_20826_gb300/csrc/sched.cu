@@ -36,6 +36,8 @@ struct Ws {
     int32_t *sc;
     // phase A (+ wanc, kept through phase B)
     uint64_t *wanc, *anc, *planes;
+    int32_t *poff;  // CTA teams: predecessor lists by node (inclusive offsets) ...
+    uint16_t *pid;  // ... and their entries
     // phase B
     uint64_t *skey;
     uint16_t *bk, *pos;
@@ -67,7 +69,7 @@ __host__ __device__ inline int pow2_ceil(int v) {
 
 // Carve a workspace for DAGs of up to vc nodes and ec edges out of `base`; returns the
 // bytes used.
-__host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec, Ws *ws) {
+__host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec, Ws *ws, bool cta = false) {
     const int W = ceil_div(vc, 64) > 0 ? ceil_div(vc, 64) : 1;
     const int P = pow2_ceil(vc > 0 ? vc : 1);
     int64_t off = 0;
@@ -102,6 +104,8 @@ __host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec,
     const int64_t xa = off;  // phases A and B keep wanc
     w.anc = (uint64_t *)take(8ll * vc * W);
     w.planes = (uint64_t *)take(8ll * 32 * W);
+    w.poff = cta ? (int32_t *)take(4ll * (vc + 1)) : nullptr;
+    w.pid = cta ? (uint16_t *)take(2ll * (ec > 0 ? ec : 1)) : nullptr;
     mark();
     off = xa;
     w.skey = (uint64_t *)take(8ll * P);
@@ -142,7 +146,7 @@ __host__ __device__ inline int64_t ws_carve(unsigned char *base, int vc, int ec,
     return align_up(end, 128);
 }
 
-int64_t sched_ws_bytes(int vc, int ec) { return ws_carve(nullptr, vc, ec, nullptr); }
+int64_t sched_ws_bytes(int vc, int ec) { return ws_carve(nullptr, vc, ec, nullptr, true); }
 
 // ------------------------------------------------------------------ per-DAG context
 struct Dag {
@@ -716,12 +720,13 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
     // ---- in-degrees (a join has at least two predecessors), one edge per thread
     for (int e = tm.t; e < (int)E; e += NT) atomicAdd(&ws.cnt[col[e]], 1);
     const int W = (V + 63) >> 6;
-    for (int i = tm.t; i < V * W; i += NT) ws.anc[i] = 0;
+    if constexpr (NT == 32)  // CTA teams write every word of the closure (pulled below)
+        for (int i = tm.t; i < V * W; i += NT) ws.anc[i] = 0;
     if (lead) sc[0] = 0;
     tm.sync();
 
-    // ---- Kahn levels, and the ancestor closure pushed along each level's out-edges:
-    //      everything that reaches u, and u itself, reaches each successor of u
+    // ---- Kahn levels, and (warp teams) the ancestor closure pushed along each level's
+    //      out-edges: everything that reaches u, and u itself, reaches each successor of u
     for (int v = tm.t; v < V; v += NT) {
         const int dg = ws.cnt[v];
         ws.indeg[v] = (uint16_t)dg;
@@ -764,13 +769,15 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
                 int s = 0;
                 if (f < total) {
                     s = col[eo + f - so];
-                    const uint64_t *au = ws.anc + (int64_t)uo * W;
-                    unsigned long long *as = (unsigned long long *)(ws.anc + (int64_t)s * W);
-                    for (int w = 0; w < W; w++) {
-                        const uint64_t y = au[w];
-                        if (y) atomicOr(&as[w], (unsigned long long)y);
+                    if constexpr (NT == 32) {  // warp teams push the closure along the edge
+                        const uint64_t *au = ws.anc + (int64_t)uo * W;
+                        unsigned long long *as = (unsigned long long *)(ws.anc + (int64_t)s * W);
+                        for (int w = 0; w < W; w++) {
+                            const uint64_t y = au[w];
+                            if (y) atomicOr(&as[w], (unsigned long long)y);
+                        }
+                        atomicOr(&as[uo >> 6], 1ull << (uo & 63));
                     }
-                    atomicOr(&as[uo >> 6], 1ull << (uo & 63));
                     rel = atomicSub(&ws.cnt[s], 1) == 1;
                 }
                 const uint32_t rm = __ballot_sync(FULL, rel);
@@ -810,16 +817,58 @@ __device__ void schedule_one(const Team<NT> &tm, const Ws &ws, const SchedArgs &
         ws.planes[i] = word;
     }
     tm.sync();
-    for (int v = tm.t; v < V; v += NT) {
-        const uint64_t *av = ws.anc + (int64_t)v * W;
-        uint64_t acc = ws.load[v];
-        for (int b = 0; b < nb; b++) {
-            uint32_t c = 0;
-            for (int w = 0; w < W; w++) c += __popcll(av[w] & ws.planes[b * W + w]);
-            acc += (uint64_t)c << b;
+    if constexpr (NT == 32) {
+        for (int v = tm.t; v < V; v += NT) {
+            const uint64_t *av = ws.anc + (int64_t)v * W;
+            uint64_t acc = ws.load[v];
+            for (int b = 0; b < nb; b++) {
+                uint32_t c = 0;
+                for (int w = 0; w < W; w++) c += __popcll(av[w] & ws.planes[b * W + w]);
+                acc += (uint64_t)c << b;
+            }
+            ws.wanc[v] = acc;
+            if (a.o.wanc) a.o.wanc[n0 + v] = (int64_t)acc;
         }
-        ws.wanc[v] = acc;
-        if (a.o.wanc) a.o.wanc[n0 + v] = (int64_t)acc;
+    } else {
+        // CTA teams: the closure pulled level by level with plain loads and stores, each
+        // thread one (node, 64-bit word) pair -- everything that reaches a predecessor p,
+        // and p itself, reaches v -- and the word's share of W^anc added right away
+        for (int v = tm.t; v < V; v += NT) {
+            ws.poff[v] = ws.indeg[v];
+            ws.wanc[v] = ws.load[v];
+        }
+        tm.sync();
+        team_scan_inplace(tm, ws.poff, V, [](uint64_t x, uint64_t y) { return x + y; }, false);
+        for (int u = tm.t; u < V; u += NT)  // ws.cnt is zero again after Kahn's pass
+            for (int e = rp[u]; e < (int)rp[u + 1]; e++) {
+                const int s = col[e];
+                ws.pid[ws.poff[s] - ws.indeg[s] + atomicAdd(&ws.cnt[s], 1)] = (uint16_t)u;
+            }
+        tm.sync();
+        for (int l = 0; l < nlev; l++) {
+            const int lb = ws.lvl_off[l], lend = (l + 1 < nlev) ? ws.lvl_off[l + 1] : V;
+            const int n_items = (lend - lb) * W;
+            for (int it = tm.t; it < n_items; it += NT) {
+                const int q = it / W, w = it - q * W;
+                const int v = ws.topo[lb + q];
+                const int pe = ws.poff[v], pb = pe - ws.indeg[v];
+                uint64_t word = 0;
+                for (int k = pb; k < pe; k++) {
+                    const int p = ws.pid[k];
+                    word |= ws.anc[(int64_t)p * W + w];
+                    if ((p >> 6) == w) word |= 1ull << (p & 63);
+                }
+                ws.anc[(int64_t)v * W + w] = word;
+                if (word) {
+                    uint64_t c = 0;
+                    for (int b = 0; b < nb; b++) c += (uint64_t)__popcll(word & ws.planes[b * W + w]) << b;
+                    atomicAdd((unsigned long long *)&ws.wanc[v], (unsigned long long)c);
+                }
+            }
+            tm.sync();
+        }
+        if (a.o.wanc)
+            for (int v = tm.t; v < V; v += NT) a.o.wanc[n0 + v] = (int64_t)ws.wanc[v];
     }
     tm.sync();
 
@@ -1283,7 +1332,7 @@ __global__ void __launch_bounds__(NT) k_sched_cta(SchedArgs a) {
     __shared__ uint64_t red[NT / 32];
     __shared__ int idx_s;
     Ws ws;
-    ws_carve(SMEM ? smem : a.gws + (int64_t)blockIdx.x * a.gws_stride, a.vcap, a.ecap, &ws);
+    ws_carve(SMEM ? smem : a.gws + (int64_t)blockIdx.x * a.gws_stride, a.vcap, a.ecap, &ws, true);
     Team<NT> tm{(int)threadIdx.x, red};
     for (;;) {
         if (threadIdx.x == 0) idx_s = atomicAdd(a.counter, 1);
