@@ -24,6 +24,8 @@
  *    outputs are valid once the caller synchronises the stream.
  *  - The caller owns every buffer it passes; the library owns the staging and scratch
  *    memory inside a context and a batch, and frees it in dagrt_destroy/dagrt_batch_free.
+ *  - A context and its batches are used from one host thread at a time: the context's
+ *    staging buffers (device and pinned host) are shared by its calls.
  */
 #ifndef DAGRT_H
 #define DAGRT_H
