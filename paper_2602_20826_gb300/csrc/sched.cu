@@ -10,6 +10,10 @@
 // Alg.2 is sequential over the groups of a DAG. Groups with few members (the common case)
 // are scheduled by one thread of the team with plain loads and stores and no team-wide
 // barrier; large groups use the whole team.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "dagrt_internal.cuh"
 #include "sched.cuh"
 
@@ -1346,14 +1350,41 @@ __global__ void __launch_bounds__(NT) k_sched_cta(SchedArgs a) {
 }
 
 // ------------------------------------------------------------------ launchers
+// Occupancy of the warp kernel per (device, dynamic shared memory), queried once per size
+// (a schedule call launches up to 16 classes; these host queries were a visible part of
+// its enqueue time).
+namespace {
+struct WarpLaunchCache {
+    std::mutex mu;
+    std::map<std::pair<int, int64_t>, int> occ;  // (device, bytes) -> CTAs per SM
+};
+WarpLaunchCache &warp_cache() {
+    static WarpLaunchCache c;
+    return c;
+}
+}  // namespace
+
 cudaError_t sched_launch_warp(const SchedArgs &a, int n_sm, cudaStream_t st) {
     const int64_t bytes = ws_carve(nullptr, a.vcap, a.ecap, nullptr) * kWarpsPerCta;
-    if (bytes > sched_smem_limit()) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_sched_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_warp, 32 * kWarpsPerCta, bytes);
-    if (e != cudaSuccess) return e;
+    {
+        WarpLaunchCache &c = warp_cache();
+        std::lock_guard<std::mutex> lock(c.mu);
+        auto it = c.occ.find({dev, bytes});
+        if (it == c.occ.end() && bytes > sched_smem_limit()) return cudaErrorInvalidValue;
+        e = cudaFuncSetAttribute(k_sched_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        if (it != c.occ.end()) {
+            per_sm = it->second;
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_warp, 32 * kWarpsPerCta, bytes);
+            if (e != cudaSuccess) return e;
+            c.occ[{dev, bytes}] = per_sm;
+        }
+    }
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = n_sm * per_sm;
     const int need = ceil_div(a.n_list, kWarpsPerCta);
