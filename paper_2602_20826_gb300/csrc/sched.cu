@@ -1396,15 +1396,15 @@ cudaError_t sched_launch_warp(const SchedArgs &a, int n_sm, cudaStream_t st) {
 
 int sched_cta_grid(int n_sm) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_cta<kCtaThreads, false>, kCtaThreads, 0) !=
-            cudaSuccess || per_sm < 1)
-        per_sm = 1;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_cta<kCtaThreadsGlobal, false>,
+                                                                        kCtaThreadsGlobal, 0);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return n_sm * per_sm;
 }
 
 cudaError_t sched_launch_cta(const SchedArgs &a, int grid, cudaStream_t st) {
     if (grid < 1 || a.n_list < 1) return cudaSuccess;
-    k_sched_cta<kCtaThreads, false><<<grid, kCtaThreads, 0, st>>>(a);
+    k_sched_cta<kCtaThreadsGlobal, false><<<grid, kCtaThreadsGlobal, 0, st>>>(a);
     return cudaGetLastError();
 }
 
