@@ -916,7 +916,9 @@ cudaError_t bound_launch(const BoundArgs &a, const ChunkArgs *ch, int n_sm, cuda
                                                                               : k_bound_tma<1, false, false>);
     for (K kern : {fast, wide}) {
         int per_sm = 0;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int mx = max_dynamic_smem(kern);
+        if (smem > mx) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;

@@ -188,4 +188,20 @@ __device__ __forceinline__ uint64_t split_size(uint64_t L, uint32_t k, uint32_t 
     return p;
 }
 
+// The largest dynamic shared memory a launch of `kern` may take on the current device: the
+// opt-in maximum per block less the kernel's static shared memory (0 on error). Kernels
+// whose launches use different sizes set their attribute to this, not to one launch's
+// size: the attribute is per function, and a captured graph node launched on its own (as
+// a profiler replays it) is checked against the attribute's current value.
+template <class F>
+inline int max_dynamic_smem(F *kern) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kern) != cudaSuccess)
+        return 0;
+    return optin - (int)fa.sharedSizeBytes;
+}
+
 }  // namespace dagrt

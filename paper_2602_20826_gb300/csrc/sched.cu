@@ -1357,6 +1357,7 @@ namespace {
 struct WarpLaunchCache {
     std::mutex mu;
     std::map<std::pair<int, int64_t>, int> occ;  // (device, bytes) -> CTAs per SM
+    std::map<int, int> max_smem;                 // device -> max_dynamic_smem(k_sched_warp)
 };
 WarpLaunchCache &warp_cache() {
     static WarpLaunchCache c;
@@ -1375,7 +1376,11 @@ cudaError_t sched_launch_warp(const SchedArgs &a, int n_sm, cudaStream_t st) {
         std::lock_guard<std::mutex> lock(c.mu);
         auto it = c.occ.find({dev, bytes});
         if (it == c.occ.end() && bytes > sched_smem_limit()) return cudaErrorInvalidValue;
-        e = cudaFuncSetAttribute(k_sched_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        auto mx = c.max_smem.find(dev);
+        if (mx == c.max_smem.end()) mx = c.max_smem.emplace(dev, max_dynamic_smem(k_sched_warp)).first;
+        if (bytes > mx->second) return cudaErrorInvalidValue;
+        // the classes differ in size: the attribute allows the largest, whatever launched last
+        e = cudaFuncSetAttribute(k_sched_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, mx->second);
         if (e != cudaSuccess) return e;
         if (it != c.occ.end()) {
             per_sm = it->second;
@@ -1419,8 +1424,9 @@ int64_t sched_smem_limit() {
 cudaError_t sched_launch_cta_smem(const SchedArgs &a, int n_sm, cudaStream_t st) {
     if (a.n_list < 1) return cudaSuccess;
     const int64_t bytes = sched_ws_bytes(a.vcap, a.ecap);
-    cudaError_t e = cudaFuncSetAttribute(k_sched_cta<kCtaThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+    const int mx = max_dynamic_smem(k_sched_cta<kCtaThreads, true>);
+    if (bytes > mx) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_sched_cta<kCtaThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sched_cta<kCtaThreads, true>, kCtaThreads, bytes);
